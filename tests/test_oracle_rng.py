@@ -1,0 +1,128 @@
+"""Pins for the oracle's random numbers (Philox4x32-10 and its transforms).
+
+Philox is checked against an independent library implementation (Triton's
+Philox, run by its CPU interpreter in a subprocess); the transforms against
+their exact definitions and distributional tests.
+"""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+from scipy import stats
+
+TRITON_SCRIPT = r"""
+import os, sys, json
+os.environ["TRITON_INTERPRET"] = "1"
+import numpy as np, torch, triton, triton.language as tl
+
+@triton.jit
+def k(c_ptr, k_ptr, o_ptr, n: tl.constexpr):
+    i = tl.arange(0, n)
+    c0 = tl.load(c_ptr + 4 * i + 0); c1 = tl.load(c_ptr + 4 * i + 1)
+    c2 = tl.load(c_ptr + 4 * i + 2); c3 = tl.load(c_ptr + 4 * i + 3)
+    k0 = tl.load(k_ptr + 2 * i + 0); k1 = tl.load(k_ptr + 2 * i + 1)
+    a, b, c, d = tl.philox_impl(c0, c1, c2, c3, k0, k1, 10)
+    tl.store(o_ptr + 4 * i + 0, a); tl.store(o_ptr + 4 * i + 1, b)
+    tl.store(o_ptr + 4 * i + 2, c); tl.store(o_ptr + 4 * i + 3, d)
+
+inp = json.loads(sys.stdin.read())
+ctr = np.array(inp["ctr"], dtype=np.uint32); key = np.array(inp["key"], dtype=np.uint32)
+n = len(ctr)
+c = torch.from_numpy(ctr.view(np.int32).copy()).view(torch.uint32)
+kk = torch.from_numpy(key.view(np.int32).copy()).view(torch.uint32)
+o = torch.zeros(4 * n, dtype=torch.uint32)
+k[(1,)](c, kk, o, n)
+print(json.dumps(o.numpy().view(np.uint32).astype(np.int64).tolist()))
+"""
+
+
+def test_philox_matches_triton_library(orc):
+    pytest.importorskip("triton")
+    rng = np.random.default_rng(123)
+    ctr = rng.integers(0, 2 ** 32, (16, 4), dtype=np.uint64).astype(np.uint32)
+    key = rng.integers(0, 2 ** 32, (16, 2), dtype=np.uint64).astype(np.uint32)
+    ctr[0] = 0
+    key[0] = 0
+    ctr[1] = 0xFFFFFFFF
+    key[1] = 0xFFFFFFFF
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    out = subprocess.run([sys.executable, "-c", TRITON_SCRIPT], input=json.dumps(
+        {"ctr": ctr.astype(np.int64).tolist(), "key": key.astype(np.int64).tolist()}),
+        capture_output=True, text=True, env=env, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    ref = np.array(json.loads(out.stdout.strip().splitlines()[-1]), dtype=np.uint64).reshape(-1, 4)
+    for i in range(len(ctr)):
+        got = orc.philox4x32_10(ctr[i], key[i])
+        assert np.array_equal(got.astype(np.uint64), ref[i]), (i, got, ref[i])
+
+
+def test_philox_counter_layout(orc):
+    # key = (seed lo, seed hi), ctr = (particle, instance, step, purpose << 16 | block)
+    seed = 0x0123456789ABCDEF
+    got = orc.philox_block(seed, 7, 3, 11, 2, 1)
+    ref = orc.philox4x32_10([7, 3, 11, (2 << 16) | 1], [0x89ABCDEF, 0x01234567])
+    assert np.array_equal(got, ref)
+
+
+def test_philox_avalanche(orc):
+    # flipping one counter bit flips about half of the 128 output bits
+    rng = np.random.default_rng(5)
+    flips = []
+    for _ in range(200):
+        c = rng.integers(0, 2 ** 32, 4, dtype=np.uint64).astype(np.uint32)
+        k = rng.integers(0, 2 ** 32, 2, dtype=np.uint64).astype(np.uint32)
+        a = orc.philox4x32_10(c, k)
+        c2 = c.copy()
+        c2[rng.integers(0, 4)] ^= np.uint32(1 << int(rng.integers(0, 32)))
+        b = orc.philox4x32_10(c2, k)
+        flips.append(sum(bin(int(x) ^ int(y)).count("1") for x, y in zip(a, b)))
+    assert abs(np.mean(flips) - 64) < 2.0
+
+
+def test_u01_exact_open_interval(orc):
+    assert orc.u01(0) == 2.0 ** -24
+    assert orc.u01(0xFFFFFFFF) == 1.0 - 2.0 ** -24
+    rng = np.random.default_rng(1)
+    for w in rng.integers(0, 2 ** 32, 1000, dtype=np.uint64):
+        u = orc.u01(int(w))
+        assert 0.0 < u < 1.0
+        assert float(np.float32(u)) == u  # exactly representable in FP32
+        assert u == ((int(w) >> 9) * 2 + 1) / 2.0 ** 24
+
+
+def test_uniform_discrete(orc):
+    # for four values the draw is the top two bits of the word
+    rng = np.random.default_rng(2)
+    ws = rng.integers(0, 2 ** 32, 20000, dtype=np.uint64)
+    vals = np.array([orc.uniform_discrete(int(w), 2, 5) for w in ws])
+    assert np.array_equal(vals, 2 + (ws >> np.uint64(30)).astype(np.int64))
+    counts = np.bincount(vals - 2, minlength=4)
+    assert stats.chisquare(counts).pvalue > 1e-4
+    assert orc.uniform_discrete(0, 2, 5) == 2 and orc.uniform_discrete(0xFFFFFFFF, 2, 5) == 5
+    assert all(orc.uniform_discrete(int(w), 1, 9) in range(1, 10) for w in ws[:1000])
+
+
+def test_box_muller_distribution(orc):
+    n = 200000
+    z = np.empty(2 * n)
+    for i in range(n):
+        w = orc.philox_block(99, i, 0, 0, 1, 0)
+        z[2 * i], z[2 * i + 1] = orc.box_muller(w[0], w[1])
+    assert abs(z.mean()) < 5 * 1.0 / np.sqrt(2 * n)
+    assert abs(z.var() - 1.0) < 5 * np.sqrt(2.0 / (2 * n))
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+    # the pair is independent: correlation of (z0, z1) is ~0
+    assert abs(np.corrcoef(z[0::2], z[1::2])[0, 1]) < 5 / np.sqrt(n)
+
+
+def test_box_muller_definition_points(orc):
+    # w = 0 for u_b gives angle 2*pi*2^-24: z0 ~ rho, z1 ~ rho * 2*pi*2^-24
+    wa = 0x80000000  # u_a = (2^22 + 0.5) / 2^23
+    ua = (2 ** 22 + 0.5) / 2 ** 23
+    rho = np.sqrt(-2 * np.log(ua))
+    z0, z1 = orc.box_muller(wa, 0)
+    assert z0 == pytest.approx(rho * np.cos(2 * np.pi * 2.0 ** -24), rel=1e-15)
+    assert z1 == pytest.approx(rho * np.sin(2 * np.pi * 2.0 ** -24), rel=1e-12)
