@@ -6,16 +6,17 @@
  * the standard systematic scheme (Kitagawa 1996; Douc, Cappé and Moulines
  * 2005) stated over integers so that ancestors are exact:
  *   m   = max_i lw_i                           (FP32 log-weights)
- *   S   = 63 - ceil(log2 N)
+ *   S   = 61 - ceil(log2 N)
  *   q_i = floor(E32(lw_i - m) * 2^S)           (u64; 0 when lw_i - m < -44.5)
- *   T   = sum_i q_i  (<= 2^63),  step = floor(T / M)
+ *   T   = sum_i q_i  (<= 2^61),  step = floor(T / M)
  *   u'  = floor(w * step / 2^32)               (w: word 0 of purpose RESAMPLE)
  *   a_k = min { j : C_j > u' + k * step },  C_j = q_0 + ... + q_j,  k = 0..M-1
  * E32 is the fixed FP32 exponential below.  It is part of the definition
  * because the integers q_i are decided in FP32 and must be the same on every
  * implementation: Cody-Waite reduction by ln 2 (Cody and Waite 1980), then the
  * degree-7 Taylor polynomial of exp on |r| <= ln(2)/2 in Horner form, every
- * step a correctly rounded FP32 multiply or fused multiply-add.
+ * step a correctly rounded FP32 multiply or fused multiply-add.  The scale
+ * 2^S keeps T below 2^61, so any prefix sum fits in 62 bits.
  */
 #include "oracle.h"
 
@@ -45,7 +46,7 @@ float orc_exp32(float d) {
 int orc_fixed_shift(int64_t N) {
   int s = 0;
   while (((int64_t)1 << s) < N) s++;
-  return 63 - s;
+  return 61 - s;
 }
 
 void orc_quantize_weights(const float* lw, int64_t N, uint64_t* q) {

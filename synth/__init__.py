@@ -114,9 +114,9 @@ def log_weights(N, seed, kind="normal", scale=3.0):
 
 
 def fixed_weights(N, seed, max_bits=40):
-    """u64 fixed-point weights (zeros included) whose sum stays below 2^63."""
+    """u64 fixed-point weights (zeros included) whose sum stays below 2^61."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    bits = min(max_bits, 62 - int(np.ceil(np.log2(max(N, 2)))))
+    bits = min(max_bits, 60 - int(np.ceil(np.log2(max(N, 2)))))
     q = rng.integers(0, 2 ** bits, N, dtype=np.uint64)
     q[rng.random(N) < 0.3] = 0
     return q

@@ -22,11 +22,11 @@ def test_exp32_accuracy(orc):
 
 
 def test_fixed_shift(orc):
-    assert orc.fixed_shift(1) == 63
-    assert orc.fixed_shift(2) == 62
-    assert orc.fixed_shift(3) == 61
-    assert orc.fixed_shift(1 << 24) == 39
-    assert orc.fixed_shift((1 << 24) + 1) == 38
+    assert orc.fixed_shift(1) == 61
+    assert orc.fixed_shift(2) == 60
+    assert orc.fixed_shift(3) == 59
+    assert orc.fixed_shift(1 << 24) == 37
+    assert orc.fixed_shift((1 << 24) + 1) == 36
 
 
 @pytest.mark.parametrize("kind", ["normal", "equal", "onehot", "sparse", "wide"])
@@ -41,7 +41,7 @@ def test_quantize_weights(orc, kind):
     assert np.all(np.abs(q[ok].astype(np.float64) / ideal[ok] - 1) < 3 * 2.0 ** -24)
     assert np.all(q[~ok].astype(np.float64) <= ideal[~ok] * (1 + 1e-6) + 1)
     assert q.max() == np.uint64(1) << np.uint64(S)
-    assert int(q.astype(object).sum()) <= 2 ** 63
+    assert int(q.astype(object).sum()) <= 2 ** 61
 
 
 def _offset(orc, seed, instance, step_t, stride):
