@@ -78,6 +78,9 @@ def lib():
             "orc_u01": (dbl, [u32]),
             "orc_box_muller": (None, [u32, u32, vp, vp]),
             "orc_uniform_discrete": (ctypes.c_int, [u32, ctypes.c_int, ctypes.c_int]),
+            "orc_ln32": (ctypes.c_float, [ctypes.c_float]),
+            "orc_cos2pi32": (ctypes.c_float, [ctypes.c_float]),
+            "orc_normal32": (ctypes.c_float, [u32, u32]),
             "orc_poly_trace": (dbl, [vp, vp, vp, i64, u64, u32, u32, vp, vp]),
             "orc_is_poly": (None, [vp, vp, vp, i64, i64, u64, u32, vp, vp, vp]),
             "orc_is_poly_indices": (None, [vp, vp, vp, i64, vp, i64, u64, u32, vp, vp, vp]),
@@ -90,7 +93,7 @@ def lib():
             "orc_resample_from_lw": (ctypes.c_int, [vp, i64, i64, u64, u32, u32, vp]),
             "orc_gather": (None, [vp, i64, vp, i64, vp]),
             "orc_kalman_logz": (dbl, [vp, vp, i64]),
-            "orc_smc_lgssm": (dbl, [vp, vp, i64, i64, u64, vp, vp, vp, vp]),
+            "orc_smc_lgssm": (dbl, [vp, vp, i64, i64, u64, ctypes.c_int, vp, vp, vp, vp]),
             "orc_blr_evidence": (dbl, [vp, vp, i64, ctypes.c_int, dbl, dbl, vp, vp]),
             "orc_poly_exact": (dbl, [vp, vp, vp, i64, vp, vp, vp]),
             "orc_enumerate": (ctypes.c_int, [ctypes.c_int, vp, i64, ctypes.c_int, vp, vp,
@@ -140,6 +143,19 @@ def box_muller(wa, wb):
     z0, z1 = ctypes.c_double(), ctypes.c_double()
     lib().orc_box_muller(int(wa), int(wb), ctypes.byref(z0), ctypes.byref(z1))
     return z0.value, z1.value
+
+
+def ln32(u):
+    return lib().orc_ln32(float(u))
+
+
+def cos2pi32(u):
+    return lib().orc_cos2pi32(float(u))
+
+
+def normal32(wa, wb):
+    """The reproducible FP32 Box-Muller draw (cosine branch) of two words."""
+    return lib().orc_normal32(int(wa), int(wb))
 
 
 def uniform_discrete(w, lo, hi):
@@ -262,15 +278,16 @@ def kalman_logz(model, y):
     return lib().orc_kalman_logz(ctypes.byref(model), _p(y), len(y))
 
 
-def smc_lgssm(model, y, N, seed):
+def smc_lgssm(model, y, N, seed, state_f32=False):
+    """Bootstrap filter; state_f32 holds state and log-weights in FP32 (the method's policy)."""
     y = _f64(y)
     T = len(y)
     ess = np.zeros(T)
     res = np.zeros(T, dtype=np.int32)
     x = np.zeros(N)
     lw = np.zeros(N)
-    logz = lib().orc_smc_lgssm(ctypes.byref(model), _p(y), T, N, seed, _p(ess), _p(res), _p(x),
-                               _p(lw))
+    logz = lib().orc_smc_lgssm(ctypes.byref(model), _p(y), T, N, seed, int(state_f32), _p(ess),
+                               _p(res), _p(x), _p(lw))
     return {"log_z": logz, "ess": ess, "resampled": res, "x": x, "lw": lw}
 
 

@@ -14,6 +14,17 @@
  *   log Z = logZ_acc + LSE(lw) - log N
  * Draws: word 0 and 1 of block 0 of (particle i, instance 0, step t, purpose
  * LGSSM_PROPAGATE) -> the cosine Box-Muller normal e_t.
+ *
+ * Precision: with state_f32 = 0 everything is FP64.  With state_f32 = 1 the
+ * particle state and log-weights are held in FP32, as the method's precision
+ * policy fixes (FP32 state and log-weights, FP64 normalisation and evidence
+ * accumulator): the normal is the reproducible FP32 Box-Muller draw
+ * orc_normal32 of the same two words, and every update below is FP32
+ * arithmetic, one rounding per operation, in the order written:
+ *   x = phi * x + q * e;   d = y - x;   lw = lw + (c + (h * d) * d)
+ * with c = -log(2 pi r^2) / 2 and h = -1 / (2 r^2) rounded to FP32.  The
+ * resampling decisions (integers) then come from the same FP32 values a
+ * particle filter in that precision holds.
  */
 #include "oracle.h"
 
@@ -44,7 +55,12 @@ double orc_kalman_logz(const orc_lgssm* m, const double* y, int64_t T) {
 }
 
 double orc_smc_lgssm(const orc_lgssm* m, const double* y, int64_t T, int64_t N, uint64_t seed,
-                     double* ess_t, int32_t* resampled_t, double* x_out, double* lw_out) {
+                     int state_f32, double* ess_t, int32_t* resampled_t, double* x_out,
+                     double* lw_out) {
+  const double two_pi = 6.283185307179586476925286766559;
+  const float phi_f = (float)m->phi, q_f = (float)m->q_sigma;
+  const float c_f = (float)(-0.5 * log(two_pi * m->r_sigma * m->r_sigma));
+  const float h_f = (float)(-1.0 / (2.0 * m->r_sigma * m->r_sigma));
   double* x = (double*)calloc((size_t)N, sizeof(double));
   double* xn = (double*)calloc((size_t)N, sizeof(double));
   double* lw = (double*)calloc((size_t)N, sizeof(double));
@@ -59,8 +75,18 @@ double orc_smc_lgssm(const orc_lgssm* m, const double* y, int64_t T, int64_t N, 
       double z0, z1;
       orc_philox_block(seed, (uint32_t)i, 0, (uint32_t)t, ORC_PURPOSE_LGSSM_PROPAGATE, 0, w);
       orc_box_muller(w[0], w[1], &z0, &z1);
-      x[i] = m->phi * x[i] + m->q_sigma * z0;
-      lw[i] += log_normal_pdf(y[t - 1], x[i], r2);
+      if (state_f32) {
+        float xf = (float)x[i], lf = (float)lw[i], zf = orc_normal32(w[0], w[1]);
+        float yf = (float)y[t - 1];
+        xf = phi_f * xf + q_f * zf;
+        float d = yf - xf;
+        lf = lf + (c_f + (h_f * d) * d);
+        x[i] = xf;
+        lw[i] = lf;
+      } else {
+        x[i] = m->phi * x[i] + m->q_sigma * z0;
+        lw[i] += log_normal_pdf(y[t - 1], x[i], r2);
+      }
     }
     double lse, ess;
     orc_lse_ess(lw, N, &lse, &ess, NULL, NULL);

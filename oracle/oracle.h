@@ -37,6 +37,9 @@ void orc_philox_block(uint64_t seed, uint32_t particle, uint32_t instance, uint3
 double orc_u01(uint32_t w);
 void orc_box_muller(uint32_t wa, uint32_t wb, double* z0, double* z1);
 int orc_uniform_discrete(uint32_t w, int lo, int hi);
+float orc_ln32(float u);
+float orc_cos2pi32(float u);
+float orc_normal32(uint32_t wa, uint32_t wb);
 
 /* ---- polynomial line-fitting model (poly.c) ---------------------------- */
 typedef struct {
@@ -91,7 +94,8 @@ typedef struct {
 
 double orc_kalman_logz(const orc_lgssm* m, const double* y, int64_t T);
 double orc_smc_lgssm(const orc_lgssm* m, const double* y, int64_t T, int64_t N, uint64_t seed,
-                     double* ess_t, int32_t* resampled_t, double* x_out, double* lw_out);
+                     int state_f32, double* ess_t, int32_t* resampled_t, double* x_out,
+                     double* lw_out);
 
 /* ---- conjugate evidence (conjugate.c) --------------------------------- */
 double orc_blr_evidence(const double* x, const double* y, int64_t L, int ncoef, double sigma,

@@ -15,6 +15,7 @@
 
 #include <math.h>
 #include <omp.h>
+#include <string.h>
 
 /* Multipliers and key increments as published by Salmon et al. (SC'11). */
 #define PHILOX_M0 0xD2511F53u
@@ -73,6 +74,77 @@ void orc_box_muller(uint32_t wa, uint32_t wb, double* z0, double* z1) {
 int orc_uniform_discrete(uint32_t w, int lo, int hi) {
   uint64_t range = (uint64_t)(hi - lo + 1);
   return lo + (int)(((uint64_t)w * range) >> 32);
+}
+
+/*
+ * FP32 standard normal with a fixed, reproducible result: the Box-Muller
+ * cosine branch z = sqrt(-2 ln u_a) cos(2 pi u_b), where every step is one
+ * correctly rounded FP32 operation (+, -, *, /, fma, sqrt, rint) in the order
+ * written, so any implementation of this definition returns the same bits.
+ *  ln u: u = m 2^e with m in [sqrt(1/2), sqrt(2)]; ln m = 2 atanh(s),
+ *        s = (m - 1)/(m + 1), atanh(s)/s = 1 + s^2/3 + s^4/5 + s^6/7 + s^8/9
+ *        (truncation < 3e-9 relative); ln u = e ln2_hi + (e ln2_lo + ln m).
+ *  cos(2 pi u): v = 4u = k + r exactly (k = rint(v), |r| <= 1/2); cos and sin
+ *        of (pi/2) r by their Taylor series to degree 10 and 9 (truncation
+ *        < 2e-9); the quadrant k mod 4 picks cos, -sin, -cos or sin.
+ * Coefficients are the FP32 roundings of the exact series coefficients.
+ */
+static float ln32(float u) {
+  uint32_t b;
+  memcpy(&b, &u, sizeof b);
+  int e = (int)((b >> 23) & 0xffu) - 127;
+  uint32_t mb = (b & 0x7fffffu) | 0x3f800000u;
+  float m;
+  memcpy(&m, &mb, sizeof m);
+  if (m > 0x1.6a09e6p+0f) { /* above sqrt(2) */
+    m = m * 0.5f;
+    e += 1;
+  }
+  float s = (m - 1.0f) / (m + 1.0f);
+  float s2 = s * s;
+  float p = 0x1.c71c72p-4f;        /* 1/9 */
+  p = fmaf(p, s2, 0x1.24924ap-3f); /* 1/7 */
+  p = fmaf(p, s2, 0x1.99999ap-3f); /* 1/5 */
+  p = fmaf(p, s2, 0x1.555556p-2f); /* 1/3 */
+  float t = s2 * p;
+  float two_s = s + s;
+  float lnm = fmaf(two_s, t, two_s);
+  float ef = (float)e;
+  return fmaf(ef, 0x1.62e4p-1f, fmaf(ef, 0x1.7f7d1cp-20f, lnm)); /* ln2 = hi + lo */
+}
+
+static float cos2pi32(float u) {
+  float v = 4.0f * u;
+  float k = rintf(v);
+  float r = v - k;
+  float r2 = r * r;
+  float sp = 0x1.507834p-13f;          /* (pi/2)^9 / 9! */
+  sp = fmaf(sp, r2, -0x1.32d2ccp-8f);  /* -(pi/2)^7 / 7! */
+  sp = fmaf(sp, r2, 0x1.466bc6p-4f);   /* (pi/2)^5 / 5! */
+  sp = fmaf(sp, r2, -0x1.4abbcep-1f);  /* -(pi/2)^3 / 3! */
+  sp = fmaf(sp, r2, 0x1.921fb6p+0f);   /* pi/2 */
+  sp = sp * r;
+  float cp = -0x1.a6d1f2p-16f;         /* -(pi/2)^10 / 10! */
+  cp = fmaf(cp, r2, 0x1.e1f506p-11f);  /* (pi/2)^8 / 8! */
+  cp = fmaf(cp, r2, -0x1.55d3c8p-6f);  /* -(pi/2)^6 / 6! */
+  cp = fmaf(cp, r2, 0x1.03c1f0p-2f);   /* (pi/2)^4 / 4! */
+  cp = fmaf(cp, r2, -0x1.3bd3ccp+0f);  /* -(pi/2)^2 / 2! */
+  cp = fmaf(cp, r2, 1.0f);
+  switch (((int)k) & 3) {
+    case 0: return cp;
+    case 1: return -sp;
+    case 2: return -cp;
+    default: return sp;
+  }
+}
+
+float orc_ln32(float u) { return ln32(u); }
+float orc_cos2pi32(float u) { return cos2pi32(u); }
+
+float orc_normal32(uint32_t wa, uint32_t wb) {
+  float ua = (float)orc_u01(wa), ub = (float)orc_u01(wb); /* exact */
+  float rho = sqrtf(-2.0f * ln32(ua));
+  return rho * cos2pi32(ub);
 }
 
 void orc_set_threads(int n) { omp_set_num_threads(n > 0 ? n : 1); }

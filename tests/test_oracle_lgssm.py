@@ -32,11 +32,12 @@ def test_kalman_matches_joint_gaussian(orc, T, phi, q, r):
     assert lz == pytest.approx(_joint_logpdf(y, phi, q, r), abs=1e-10)
 
 
-def test_smc_converges_to_kalman(orc):
+@pytest.mark.parametrize("state_f32", [False, True])
+def test_smc_converges_to_kalman(orc, state_f32):
     model = orc.lgssm_model()
     y = synth.lgssm_dataset(50, 2)
     exact = orc.kalman_logz(model, y)
-    zs = np.array([orc.smc_lgssm(model, y, 1 << 12, s)["log_z"] for s in range(16)])
+    zs = np.array([orc.smc_lgssm(model, y, 1 << 12, s, state_f32)["log_z"] for s in range(16)])
     se = zs.std(ddof=1) / math.sqrt(len(zs))
     # SMC's evidence estimate is unbiased in Z, so log Z is biased low by ~var/2
     bias = zs.var(ddof=1) / 2
@@ -62,3 +63,14 @@ def test_smc_single_particle_is_prior_path(orc):
     out = orc.smc_lgssm(model, y, 1, 3)
     assert out["resampled"].sum() == 0
     assert out["log_z"] == pytest.approx(out["lw"][0], abs=1e-12)
+
+
+def test_smc_fp32_state_is_rounded_fp64_state(orc):
+    # one step without resampling: the FP32 state is the FP64 update in FP32 rounding
+    model = orc.lgssm_model()
+    y = synth.lgssm_dataset(1, 3)
+    a = orc.smc_lgssm(model, y, 64, 5, False)
+    b = orc.smc_lgssm(model, y, 64, 5, True)
+    assert np.allclose(a["x"], b["x"], rtol=3e-7, atol=1e-7)
+    assert np.allclose(a["lw"], b["lw"], rtol=1e-6, atol=1e-6)
+    assert np.all(b["x"] == b["x"].astype(np.float32))

@@ -126,3 +126,25 @@ def test_box_muller_definition_points(orc):
     z0, z1 = orc.box_muller(wa, 0)
     assert z0 == pytest.approx(rho * np.cos(2 * np.pi * 2.0 ** -24), rel=1e-15)
     assert z1 == pytest.approx(rho * np.sin(2 * np.pi * 2.0 ** -24), rel=1e-12)
+
+
+def test_normal32_is_box_muller_to_fp32_accuracy(orc):
+    rng = np.random.default_rng(17)
+    ws = rng.integers(0, 2 ** 32, (20000, 2), dtype=np.uint64)
+    got = np.array([orc.normal32(int(a), int(b)) for a, b in ws], dtype=np.float64)
+    ref = np.array([orc.box_muller(int(a), int(b))[0] for a, b in ws])
+    rho = np.sqrt(-2 * np.log([orc.u01(int(a)) for a in ws[:, 0]]))
+    assert np.all(np.abs(got - ref) <= 8 * 2.0 ** -24 * (rho + np.abs(ref)))
+    assert np.all(got == got.astype(np.float32))
+
+
+def test_ln32_and_cos2pi32_accuracy(orc):
+    u = np.concatenate([(np.arange(1, 2 ** 14) * 2 + 1) / 2.0 ** 15,
+                        ((np.arange(0, 2 ** 23, 997) + 0.5) / 2.0 ** 23)]).astype(np.float32)
+    ln = np.array([orc.ln32(v) for v in u], dtype=np.float64)
+    assert np.all(np.abs(ln - np.log(u.astype(np.float64))) <= 4 * 2.0 ** -24 * np.maximum(
+        np.abs(np.log(u.astype(np.float64))), 1e-6) + 2.0 ** -25 * 0.7)
+    cs = np.array([orc.cos2pi32(v) for v in u], dtype=np.float64)
+    assert np.all(np.abs(cs - np.cos(2 * np.pi * u.astype(np.float64))) <= 4e-7)
+    assert orc.cos2pi32(0.25) == 0.0 or abs(orc.cos2pi32(0.25)) < 1e-7
+    assert orc.cos2pi32(0.5) == -1.0 and orc.ln32(1.0) == 0.0
