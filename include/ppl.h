@@ -1,0 +1,206 @@
+/*
+ * ppl.h -- C ABI of the GB300 particle-inference library (libppl.so).
+ *
+ * The library runs the data-parallel hot path of likelihood-weighting
+ * importance sampling (§3.6.2): many particles each run one execution trace of
+ * a model function, where `sample` draws from a built-in distribution and
+ * `factor` adds to the trace's log-weight (§3.4, Fig. 2); the log-weights are
+ * normalised by log-sum-exp; sequential Monte Carlo (the particle methods named
+ * as future work in §6) adds systematic resampling; the weighted empirical
+ * posterior is reduced to the summary the line-fitting example asks for
+ * (Fig. 1, §1.1).
+ *
+ * Conventions shared by every entry point:
+ *  - Buffers marked [dev] are device memory owned by the caller; [host] are
+ *    host memory.  Nothing is allocated on these paths.
+ *  - `ws` is a caller-allocated device workspace of `ws_bytes` bytes, at least
+ *    ppl_workspace_size(...) for the largest call it serves, 256-byte aligned.
+ *    One workspace must not be used by two calls that run concurrently.
+ *  - Calls are stream-ordered and asynchronous on `stream` (a cudaStream_t;
+ *    NULL is the legacy default stream) unless stated otherwise.
+ *  - A return value reports argument errors and launch failures.  Errors found
+ *    on the device (NaN log-weights, an expired bounded wait, empty weights)
+ *    are recorded in the workspace status word and in the `status` field of a
+ *    result struct; read them with ppl_workspace_status after the stream
+ *    reaches the call.
+ *  - Random draws come from Philox4x32-10 (Salmon et al., SC'11) keyed by
+ *    `seed`, with counter (particle, instance, step, purpose << 16 | block):
+ *    results do not depend on launch configuration or control flow.
+ */
+#ifndef PPL_H
+#define PPL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* ppl_stream; /* cudaStream_t */
+
+typedef enum {
+  PPL_OK = 0,
+  PPL_EINVAL = 1,   /* invalid argument (null pointer, bad size, workspace too small) */
+  PPL_ENOMEM = 2,   /* reserved: the library never allocates on these paths */
+  PPL_ECUDA = 3,    /* a CUDA launch or call failed */
+  PPL_ENAN = 4,     /* a log-weight was NaN */
+  PPL_EEMPTY = 5,   /* every weight is zero (all log-weights -inf) */
+  PPL_ETIMEOUT = 6  /* a bounded device-side wait expired */
+} ppl_status;
+
+typedef enum { PPL_MODEL_POLY = 1, PPL_MODEL_LGSSM = 2 } ppl_model_id;
+
+/* Model registry entry.  Fields a model does not use are ignored.
+ *  PPL_MODEL_POLY (Fig. 1): n ~ uniform-discrete(min_deg, max_deg), at most 4
+ *    values; n + coef_offset coefficients (at most 6) ~ normal(0, prior_sigma);
+ *    factor(-sum_l (y_l - f(x_l))^2 / (2 obs_sigma^2)), f(x) = sum_k c_k x^k.
+ *  PPL_MODEL_LGSSM: x_0 = 0, x_t = phi x_{t-1} + q_sigma e_t; observe(normal(x_t,
+ *    obs_sigma), y_t) adds the normalised log-density (§3.4, Fig. 2). */
+typedef struct {
+  int32_t id;
+  int32_t min_deg, max_deg, coef_offset;
+  float obs_sigma;
+  float prior_sigma;
+  float phi, q_sigma;
+} ppl_model;
+
+/* Observed data set [dev]: x[len], y[len] in FP32. */
+typedef struct {
+  const float* x;
+  const float* y;
+  int64_t len;
+} ppl_data;
+
+/* One line-fitting particle, 32 bytes: the coefficients (zero beyond the
+ * trace's count), the sampled degree, and the index of the trace it came from. */
+typedef struct {
+  float c[6];
+  int32_t n;
+  uint32_t origin;
+} ppl_poly_particle;
+
+/* Posterior summary of a weighted population (§3.6.2, Fig. 1).  FP64.
+ *  log_z   = lse - log N: estimate of the evidence E_prior[exp(sum of factors)]
+ *  ess     = (sum w)^2 / sum w^2
+ *  argmax  = the mode: index of the highest log-weight (lowest index on ties)
+ *  p_n[d]  = posterior mass of degree min_deg + d; map_deg its argmax
+ *  mean_c  = weighted mean coefficients, zero beyond each trace's count
+ *  deg_mean/deg_var[d][k] = weighted mean/variance of c_k among degree min_deg + d
+ *  deg_max_lw/deg_argmax  = best trace of each degree (-inf / -1 if none) */
+typedef struct {
+  double log_z, lse, ess, max_lw;
+  int64_t argmax, n_particles;
+  int32_t map_deg, n_deg;
+  double p_n[4];
+  double mean_c[6];
+  double deg_mean[4][6];
+  double deg_var[4][6];
+  double deg_max_lw[4];
+  int64_t deg_argmax[4];
+  int32_t status, pad;
+} ppl_is_result;
+
+/* Readable name of a status code.  Never NULL. */
+const char* ppl_status_string(int32_t status);
+
+/* Workspace bytes needed by any call below for this model and sizes
+ * (n_particles particles, data_len data points or time steps).  Returns 0 for
+ * invalid arguments. */
+size_t ppl_workspace_size(const ppl_model* model, int64_t n_particles, int64_t data_len);
+
+/* Synchronise `stream` and return the device-side status recorded in `ws`
+ * by the calls issued before (PPL_OK if none failed). */
+ppl_status ppl_workspace_status(const void* ws, ppl_stream stream);
+
+/* Likelihood weighting (§3.6.2) on the line-fitting model (Fig. 1): particle i
+ * runs one trace, lw_i = sum of its factors; the population is normalised and
+ * reduced into *out_dev [dev].  lw_out [dev, n_particles] and particles_out
+ * [dev, n_particles] are optional (NULL to skip).  1 <= n_particles < 2^31;
+ * data->len >= 0. */
+ppl_status ppl_infer_is(const ppl_model* model, const ppl_data* data, int64_t n_particles,
+                        uint64_t seed, ppl_is_result* out_dev, float* lw_out,
+                        ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,
+                        ppl_stream stream);
+
+/* The two stages ppl_infer_is runs, for callers that time or skip them.
+ * ppl_trace_is: the traces of instance `instance` (counter field) with the
+ * normalisation fused in; fills log_z, lse, ess, max_lw, argmax and the
+ * per-degree bests of *out_dev and leaves the statistics in `ws`.
+ * ppl_posterior_finish: the posterior pass (p_n, mean_c, deg_mean, deg_var,
+ * map_deg) over the same population, using the statistics a ppl_trace_is on
+ * the same `ws` left; particles NULL regenerates the draws from their counters,
+ * lw NULL reads the log-weights ppl_trace_is kept in `ws`. */
+ppl_status ppl_trace_is(const ppl_model* model, const ppl_data* data, int64_t n_particles,
+                        uint64_t seed, uint32_t instance, ppl_is_result* out_dev, float* lw_out,
+                        ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,
+                        ppl_stream stream);
+ppl_status ppl_posterior_finish(const ppl_model* model, const ppl_poly_particle* particles,
+                                const float* lw, int64_t n_particles, uint64_t seed,
+                                uint32_t instance, ppl_is_result* out_dev, void* ws,
+                                size_t ws_bytes, ppl_stream stream);
+
+/* Same as ppl_infer_is with the data and the result in host memory: copies x,
+ * y in, runs, copies the summary out, and synchronises `stream` before it
+ * returns.  The workspace must also hold the data (see ppl_workspace_size). */
+ppl_status ppl_infer_is_host(const ppl_model* model, const float* x_host, const float* y_host,
+                             int64_t data_len, int64_t n_particles, uint64_t seed,
+                             ppl_is_result* out_host, void* ws, size_t ws_bytes,
+                             ppl_stream stream);
+
+/* Log-sum-exp normalisation (§3.6.2) of lw[n] [dev, FP32]: writes FP64
+ * out_dev[0] = LSE, out_dev[1] = ESS, out_dev[2] = max lw, and the argmax (lowest
+ * index on ties) as a double in out_dev[3].  NaN -> PPL_ENAN status; all -inf ->
+ * PPL_EEMPTY status. */
+ppl_status ppl_logsumexp(const float* lw, int64_t n, double* out_dev, void* ws, size_t ws_bytes,
+                         ppl_stream stream);
+
+/* Systematic resampling with 64-bit fixed-point weights.  Exactly one of lw
+ * [dev, FP32, n] and q_fixed [dev, u64, n] is non-NULL.  From lw:
+ * q_i = floor(E32(lw_i - max lw) * 2^(61 - ceil(log2 n))), E32 the library's
+ * fixed FP32 exponential; q_fixed must sum to at most 2^61.  With T = sum q,
+ * step = floor(T / m) and u = floor(w * step / 2^32) (w: word 0 of counter
+ * (0, instance, t, RESAMPLE)), ancestors[k] [dev, m] = min{j : q_0 + .. + q_j >
+ * u + k * step}.  The prefix sums are exact, so ancestors are bit-exact. */
+ppl_status ppl_resample(const float* lw, const uint64_t* q_fixed, int64_t n, int64_t m,
+                        uint64_t seed, uint32_t instance, uint32_t t, int32_t* ancestors,
+                        void* ws, size_t ws_bytes, ppl_stream stream);
+
+/* Gather of the resampled particle state: state_out[k] = state_in[ancestors[k]]
+ * for k < m, records of stride_bytes bytes [dev]; state_in holds n_in records.
+ * An ancestor outside [0, n_in) yields a zero-filled record instead of a read
+ * out of bounds.  stride_bytes > 0; in and out must not overlap. */
+ppl_status ppl_gather(const void* state_in, int64_t n_in, int64_t stride_bytes,
+                      const int32_t* ancestors, int64_t m, void* state_out, ppl_stream stream);
+
+/* One step t >= 1 of the bootstrap particle filter on PPL_MODEL_LGSSM with
+ * adaptive resampling, over x[n], lw[n] [dev, FP32].  Propagates every
+ * particle, adds observe(normal(x, obs_sigma), y_t), computes ESS; if
+ * ESS < n/2 it adds LSE - log n to *logz_acc [dev, FP64], resamples x with
+ * ppl_resample's scheme (instance 0, step t) and zeroes lw.  Writes
+ * *resampled [dev] = 1 or 0 and logz_est[0] [dev, FP64] = logz_acc + LSE(lw) -
+ * log n, the running evidence estimate; logz_est[1] = ESS before resampling. */
+ppl_status ppl_smc_step(const ppl_model* model, float y_t, int32_t t, uint64_t seed, float* x,
+                        float* lw, int64_t n, double* logz_acc, int32_t* resampled,
+                        double* logz_est, void* ws, size_t ws_bytes, ppl_stream stream);
+
+/* Posterior summary (as ppl_infer_is) of an existing weighted population of
+ * line-fitting particles [dev] with log-weights lw [dev]; lw == NULL means
+ * equal weights.  Writes *out_dev [dev]. */
+ppl_status ppl_posterior_reduce(const ppl_model* model, const ppl_poly_particle* particles,
+                                const float* lw, int64_t n, ppl_is_result* out_dev, void* ws,
+                                size_t ws_bytes, ppl_stream stream);
+
+/* The raw random words behind every `sample` (§3.4): out_dev [dev, u32,
+ * 16-byte aligned] receives, for particle i < n_particles and block j <
+ * n_blocks, the four Philox4x32-10 words of counter (i, instance, step,
+ * purpose << 16 | j) at out_dev[(i * n_blocks + j) * 4 ...].  Purposes: 1 line-
+ * fitting trace, 2 state-space propagation, 3 resampling offset. */
+ppl_status ppl_rng_words(uint64_t seed, uint32_t instance, uint32_t step, uint32_t purpose,
+                         int64_t n_particles, int32_t n_blocks, uint32_t* out_dev,
+                         ppl_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PPL_H */

@@ -1,0 +1,333 @@
+"""Python binding of libppl.so (include/ppl.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: PyTorch provides device memory and the current CUDA
+stream, the library does the work.  If libppl.so has not been built the
+binding raises; there is no CPU fallback.
+"""
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libppl.so")
+_LIB = None
+
+PPL_OK, PPL_EINVAL, PPL_ENOMEM, PPL_ECUDA, PPL_ENAN, PPL_EEMPTY, PPL_ETIMEOUT = range(7)
+PPL_MODEL_POLY, PPL_MODEL_LGSSM = 1, 2
+POLY_RECORD_FLOATS = 8  # ppl_poly_particle: c[6], n (int32 bits), origin (uint32 bits)
+
+
+class PplError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {ppl_status_string(status)} ({status})")
+
+
+class PplModel(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_int32), ("min_deg", ctypes.c_int32),
+                ("max_deg", ctypes.c_int32), ("coef_offset", ctypes.c_int32),
+                ("obs_sigma", ctypes.c_float), ("prior_sigma", ctypes.c_float),
+                ("phi", ctypes.c_float), ("q_sigma", ctypes.c_float)]
+
+
+class PplData(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("len", ctypes.c_int64)]
+
+
+class PplIsResult(ctypes.Structure):
+    _fields_ = [("log_z", ctypes.c_double), ("lse", ctypes.c_double), ("ess", ctypes.c_double),
+                ("max_lw", ctypes.c_double), ("argmax", ctypes.c_int64),
+                ("n_particles", ctypes.c_int64), ("map_deg", ctypes.c_int32),
+                ("n_deg", ctypes.c_int32), ("p_n", ctypes.c_double * 4),
+                ("mean_c", ctypes.c_double * 6), ("deg_mean", (ctypes.c_double * 6) * 4),
+                ("deg_var", (ctypes.c_double * 6) * 4), ("deg_max_lw", ctypes.c_double * 4),
+                ("deg_argmax", ctypes.c_int64 * 4), ("status", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {
+            "log_z": self.log_z, "lse": self.lse, "ess": self.ess, "max_lw": self.max_lw,
+            "argmax": self.argmax, "n_particles": self.n_particles, "map_deg": self.map_deg,
+            "n_deg": self.n_deg, "p_n": np.array(self.p_n[:]),
+            "mean_c": np.array(self.mean_c[:]),
+            "deg_mean": np.array([r[:] for r in self.deg_mean]),
+            "deg_var": np.array([r[:] for r in self.deg_var]),
+            "deg_max_lw": np.array(self.deg_max_lw[:]),
+            "deg_argmax": np.array(self.deg_argmax[:]), "status": self.status,
+        }
+
+
+RESULT_BYTES = ctypes.sizeof(PplIsResult)
+
+_SIGS = {
+    "ppl_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
+    "ppl_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]),
+    "ppl_workspace_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "ppl_infer_is": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                    ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                    ctypes.c_void_p]),
+    "ppl_trace_is": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                    ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_size_t, ctypes.c_void_p]),
+    "ppl_posterior_finish": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                            ctypes.c_void_p]),
+    "ppl_infer_is_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                         ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                         ctypes.c_void_p]),
+    "ppl_logsumexp": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "ppl_resample": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                    ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
+                                    ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_size_t, ctypes.c_void_p]),
+    "ppl_gather": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                  ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                  ctypes.c_void_p]),
+    "ppl_smc_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_float, ctypes.c_int32,
+                                    ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                    ctypes.c_void_p]),
+    "ppl_rng_words": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                     ctypes.c_uint32, ctypes.c_int64, ctypes.c_int32,
+                                     ctypes.c_void_p, ctypes.c_void_p]),
+    "ppl_posterior_reduce": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_size_t, ctypes.c_void_p]),
+}
+
+
+def exported_symbols():
+    """Names the binding expects libppl.so to export."""
+    return list(_SIGS)
+
+
+def lib():
+    """Load libppl.so; raises if it has not been built (no fallback)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libppl.so is not built ({LIB_PATH}); run "
+                               "paper_2010_08454_gb300/build.py or __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def _check(status, where):
+    if status != PPL_OK:
+        raise PplError(status, where)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev_f32(t, name):
+    if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    return t
+
+
+def ppl_status_string(status):
+    return lib().ppl_status_string(int(status)).decode()
+
+
+def poly_model(min_deg=2, max_deg=5, coef_offset=1, obs_sigma=0.5, prior_sigma=10.0):
+    return PplModel(PPL_MODEL_POLY, min_deg, max_deg, coef_offset, obs_sigma, prior_sigma, 0.0,
+                    0.0)
+
+
+def lgssm_model(phi=0.9, q_sigma=1.0, obs_sigma=0.5):
+    return PplModel(PPL_MODEL_LGSSM, 0, 0, 0, obs_sigma, 0.0, phi, q_sigma)
+
+
+def ppl_workspace_size(model, n_particles, data_len=0):
+    return int(lib().ppl_workspace_size(ctypes.byref(model), int(n_particles), int(data_len)))
+
+
+def workspace(model, n_particles, data_len=0, device="cuda"):
+    """A device workspace big enough for every call on this many particles."""
+    n = ppl_workspace_size(model, n_particles, data_len)
+    if n == 0:
+        raise ValueError("invalid workspace request")
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def ppl_workspace_status(ws, stream=None):
+    return int(lib().ppl_workspace_status(_ptr(ws), _stream(stream)))
+
+
+def result_tensor(device="cuda"):
+    return torch.zeros(RESULT_BYTES, dtype=torch.uint8, device=device)
+
+
+def read_result(res_dev):
+    """Copy a device ppl_is_result to the host (synchronises) and decode it."""
+    raw = res_dev.detach().cpu().numpy().tobytes()
+    return PplIsResult.from_buffer_copy(raw).as_dict()
+
+
+def ppl_infer_is(model, x, y, n_particles, seed, out=None, lw_out=None, particles_out=None,
+                 ws=None, stream=None):
+    """Likelihood weighting on the line-fitting model; returns the device result buffer."""
+    _dev_f32(x, "x")
+    _dev_f32(y, "y")
+    if ws is None:
+        ws = workspace(model, n_particles, x.numel(), x.device)
+    if out is None:
+        out = result_tensor(x.device)
+    data = PplData(x.data_ptr(), y.data_ptr(), x.numel())
+    st = lib().ppl_infer_is(ctypes.byref(model), ctypes.byref(data), int(n_particles),
+                            ctypes.c_uint64(seed), _ptr(out), _ptr(lw_out), _ptr(particles_out),
+                            _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "ppl_infer_is")
+    return out
+
+
+def ppl_trace_is(model, x, y, n_particles, seed, instance=0, out=None, lw_out=None,
+                 particles_out=None, ws=None, stream=None):
+    """Traces + fused normalisation (first stage of ppl_infer_is)."""
+    _dev_f32(x, "x")
+    _dev_f32(y, "y")
+    if ws is None:
+        ws = workspace(model, n_particles, x.numel(), x.device)
+    if out is None:
+        out = result_tensor(x.device)
+    data = PplData(x.data_ptr(), y.data_ptr(), x.numel())
+    st = lib().ppl_trace_is(ctypes.byref(model), ctypes.byref(data), int(n_particles),
+                            ctypes.c_uint64(seed), int(instance), _ptr(out), _ptr(lw_out),
+                            _ptr(particles_out), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "ppl_trace_is")
+    return out
+
+
+def ppl_posterior_finish(model, n_particles, seed, out, ws, instance=0, particles=None,
+                         lw=None, stream=None):
+    """Posterior pass after ppl_trace_is on the same workspace (second stage)."""
+    st = lib().ppl_posterior_finish(ctypes.byref(model), _ptr(particles), _ptr(lw),
+                                    int(n_particles), ctypes.c_uint64(seed), int(instance),
+                                    _ptr(out), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "ppl_posterior_finish")
+    return out
+
+
+def ppl_infer_is_host(model, x_host, y_host, n_particles, seed, ws, stream=None):
+    """The same with host (preferably pinned) inputs and a host result; synchronises."""
+    res = PplIsResult()
+    st = lib().ppl_infer_is_host(ctypes.byref(model), ctypes.c_void_p(x_host.data_ptr()),
+                                 ctypes.c_void_p(y_host.data_ptr()), x_host.numel(),
+                                 int(n_particles), ctypes.c_uint64(seed), ctypes.byref(res),
+                                 _ptr(ws), ws.numel(), _stream(stream))
+    if st not in (PPL_OK, PPL_ENAN, PPL_EEMPTY, PPL_ETIMEOUT):
+        _check(st, "ppl_infer_is_host")
+    return res.as_dict()
+
+
+def ppl_logsumexp(lw, out=None, ws=None, stream=None):
+    """[LSE, ESS, max, argmax] in a float64 device tensor."""
+    _dev_f32(lw, "lw")
+    if ws is None:
+        ws = workspace(poly_model(), lw.numel(), 0, lw.device)
+    if out is None:
+        out = torch.empty(4, dtype=torch.float64, device=lw.device)
+    st = lib().ppl_logsumexp(_ptr(lw), lw.numel(), _ptr(out), _ptr(ws), ws.numel(),
+                             _stream(stream))
+    _check(st, "ppl_logsumexp")
+    return out
+
+
+def ppl_resample(m, seed, instance=0, t=0, lw=None, q_fixed=None, ancestors=None, ws=None,
+                 stream=None):
+    """Systematic resampling; returns int32 ancestors[m] on the device."""
+    src = lw if lw is not None else q_fixed
+    n = src.numel()
+    if lw is not None:
+        _dev_f32(lw, "lw")
+    elif not (q_fixed.is_cuda and q_fixed.dtype in (torch.int64, torch.uint64)):
+        raise ValueError("q_fixed must be a 64-bit integer CUDA tensor")
+    if ws is None:
+        ws = workspace(poly_model(), n, 0, src.device)
+    if ancestors is None:
+        ancestors = torch.empty(m, dtype=torch.int32, device=src.device)
+    st = lib().ppl_resample(_ptr(lw), _ptr(q_fixed), n, int(m), ctypes.c_uint64(seed),
+                            int(instance), int(t), _ptr(ancestors), _ptr(ws), ws.numel(),
+                            _stream(stream))
+    _check(st, "ppl_resample")
+    return ancestors
+
+
+def ppl_gather(state_in, ancestors, state_out=None, stream=None):
+    """state_out[k] = state_in[ancestors[k]] over the leading dimension."""
+    if not state_in.is_contiguous():
+        raise ValueError("state_in must be contiguous")
+    m = ancestors.numel()
+    stride = state_in[0].numel() * state_in.element_size() if state_in.dim() > 1 else \
+        state_in.element_size()
+    if state_out is None:
+        state_out = torch.empty((m,) + tuple(state_in.shape[1:]), dtype=state_in.dtype,
+                                device=state_in.device)
+    st = lib().ppl_gather(_ptr(state_in), state_in.shape[0], stride, _ptr(ancestors), m,
+                          _ptr(state_out), _stream(stream))
+    _check(st, "ppl_gather")
+    return state_out
+
+
+def ppl_smc_step(model, y_t, t, seed, x, lw, logz_acc, resampled, logz_est, ws, stream=None):
+    """One bootstrap-filter step on the device state (x, lw, logz_acc, resampled, logz_est)."""
+    st = lib().ppl_smc_step(ctypes.byref(model), float(y_t), int(t), ctypes.c_uint64(seed),
+                            _ptr(x), _ptr(lw), x.numel(), _ptr(logz_acc), _ptr(resampled),
+                            _ptr(logz_est), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "ppl_smc_step")
+
+
+def ppl_rng_words(seed, instance, step, purpose, n_particles, n_blocks, out=None, stream=None):
+    """uint32 words [n_particles, n_blocks, 4] on the device (as int32 storage)."""
+    if out is None:
+        out = torch.empty((n_particles, n_blocks, 4), dtype=torch.int32, device="cuda")
+    st = lib().ppl_rng_words(ctypes.c_uint64(seed), int(instance), int(step), int(purpose),
+                             int(n_particles), int(n_blocks), _ptr(out), _stream(stream))
+    _check(st, "ppl_rng_words")
+    return out
+
+
+def ppl_posterior_reduce(model, particles, lw=None, out=None, ws=None, stream=None):
+    n = particles.shape[0]
+    if ws is None:
+        ws = workspace(model, n, 0, particles.device)
+    if out is None:
+        out = result_tensor(particles.device)
+    st = lib().ppl_posterior_reduce(ctypes.byref(model), _ptr(particles), _ptr(lw), n,
+                                    _ptr(out), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "ppl_posterior_reduce")
+    return out
+
+
+def poly_particles(n, device="cuda"):
+    """An uninitialised [n, 8] float32 buffer of ppl_poly_particle records."""
+    return torch.empty((n, POLY_RECORD_FLOATS), dtype=torch.float32, device=device)
+
+
+def decode_particles(p):
+    """(c[n, 6] float32, degree[n] int32, origin[n] int64) of a record buffer."""
+    c = p[:, :6]
+    deg = p[:, 6].contiguous().view(torch.int32)
+    origin = p[:, 7].contiguous().view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    return c, deg, origin

@@ -1,0 +1,300 @@
+// C ABI of libppl.so (declared in include/ppl.h): argument checks, workspace
+// layout and the launch sequence of every entry point.  No entry point
+// allocates memory; every launch is stream-ordered on the caller's stream.
+#include <math.h>
+#include <string.h>
+
+#include "kernels.h"
+#include "poly.cuh"
+
+namespace ppl {
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr size_t kHeaderBytes = 512;
+constexpr int64_t kMaxParticles = 0x7fffffffll;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+// Header and tile status words are contiguous so one memset clears both.
+WsLayout layout(int64_t n, int64_t data_len) {
+  WsLayout w;
+  size_t off = 0;
+  w.header = off;
+  off += kHeaderBytes;
+  w.tiles = off;
+  off += align_up((size_t)scan_tiles(std::max<int64_t>(n, 1)) * sizeof(uint64_t));
+  w.partials = off;
+  off += align_up(partials_bytes());
+  w.prefix = off;
+  off += align_up((size_t)n * sizeof(uint64_t));
+  w.lw = off;
+  off += align_up((size_t)n * sizeof(float));
+  w.scratch = off;
+  off += std::max(align_up((size_t)n * sizeof(int32_t)) + align_up((size_t)n * sizeof(float)),
+                  align_up((size_t)std::max<int64_t>(data_len, 0) * 2 * sizeof(float)));
+  w.total = off;
+  return w;
+}
+
+struct Ws {
+  char* base;
+  WsLayout l;
+  WsHeader* hdr() const { return reinterpret_cast<WsHeader*>(base + l.header); }
+  uint64_t* tiles() const { return reinterpret_cast<uint64_t*>(base + l.tiles); }
+  void* partials() const { return base + l.partials; }
+  uint64_t* prefix() const { return reinterpret_cast<uint64_t*>(base + l.prefix); }
+  float* lw() const { return reinterpret_cast<float*>(base + l.lw); }
+  char* scratch() const { return base + l.scratch; }
+};
+
+ppl_status check_ws(void* ws, size_t ws_bytes, int64_t n, int64_t data_len, Ws* out) {
+  if (!ws) return PPL_EINVAL;
+  if (reinterpret_cast<uintptr_t>(ws) % kAlign) return PPL_EINVAL;
+  out->base = static_cast<char*>(ws);
+  out->l = layout(n, data_len);
+  if (ws_bytes < out->l.total) return PPL_EINVAL;
+  return PPL_OK;
+}
+
+ppl_status cuda_status(cudaError_t e) { return e == cudaSuccess ? PPL_OK : PPL_ECUDA; }
+
+// Clear the header (status, tickets, tile counters) and, when `tiles`, the
+// scan tile status words.
+ppl_status reset_ws(const Ws& w, bool tiles, cudaStream_t s) {
+  const size_t bytes = tiles ? (w.l.partials - w.l.header) : kHeaderBytes;
+  return cuda_status(cudaMemsetAsync(w.base + w.l.header, 0, bytes, s));
+}
+
+ppl_status poly_params(const ppl_model* m, PolyParams* p) {
+  if (!m || m->id != PPL_MODEL_POLY) return PPL_EINVAL;
+  const int n_deg = m->max_deg - m->min_deg + 1;
+  if (m->min_deg < 0 || n_deg < 1 || n_deg > kMaxDegrees) return PPL_EINVAL;
+  if (m->coef_offset < 0 || m->min_deg + m->coef_offset < 0 ||
+      m->max_deg + m->coef_offset > kMaxCoef)
+    return PPL_EINVAL;
+  if (!(m->obs_sigma > 0.0f) || !isfinite(m->obs_sigma) || !isfinite(m->prior_sigma))
+    return PPL_EINVAL;
+  p->min_deg = m->min_deg;
+  p->n_deg = n_deg;
+  p->coef_offset = m->coef_offset;
+  p->prior_sigma = m->prior_sigma;
+  p->neg_half_inv_var = (float)(-1.0 / (2.0 * (double)m->obs_sigma * (double)m->obs_sigma));
+  return PPL_OK;
+}
+
+#define PPL_TRY(expr)                      \
+  do {                                     \
+    const ppl_status _st = (expr);         \
+    if (_st != PPL_OK) return _st;         \
+  } while (0)
+
+}  // namespace
+}  // namespace ppl
+
+using namespace ppl;
+
+extern "C" {
+
+const char* ppl_status_string(int32_t status) {
+  switch (status) {
+    case PPL_OK: return "ok";
+    case PPL_EINVAL: return "invalid argument";
+    case PPL_ENOMEM: return "out of memory";
+    case PPL_ECUDA: return "CUDA error";
+    case PPL_ENAN: return "NaN log-weight";
+    case PPL_EEMPTY: return "all weights are zero";
+    case PPL_ETIMEOUT: return "bounded device wait expired";
+    default: return "unknown status";
+  }
+}
+
+size_t ppl_workspace_size(const ppl_model* model, int64_t n_particles, int64_t data_len) {
+  if (!model || n_particles < 1 || n_particles > kMaxParticles || data_len < 0) return 0;
+  return layout(n_particles, data_len).total;
+}
+
+ppl_status ppl_workspace_status(const void* ws, ppl_stream stream) {
+  if (!ws) return PPL_EINVAL;
+  int32_t st = 0;
+  if (cudaMemcpyAsync(&st, ws, sizeof(st), cudaMemcpyDeviceToHost, (cudaStream_t)stream) !=
+      cudaSuccess)
+    return PPL_ECUDA;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return PPL_ECUDA;
+  return (ppl_status)st;
+}
+
+ppl_status ppl_trace_is(const ppl_model* model, const ppl_data* data, int64_t n_particles,
+                        uint64_t seed, uint32_t instance, ppl_is_result* out_dev, float* lw_out,
+                        ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,
+                        ppl_stream stream) {
+  PolyParams p;
+  PPL_TRY(poly_params(model, &p));
+  if (!data || data->len < 0 || (data->len > 0 && (!data->x || !data->y))) return PPL_EINVAL;
+  if (n_particles < 1 || n_particles > kMaxParticles || !out_dev) return PPL_EINVAL;
+  if (particles_out && (reinterpret_cast<uintptr_t>(particles_out) & 15)) return PPL_EINVAL;
+  Ws w;
+  PPL_TRY(check_ws(ws, ws_bytes, n_particles, data->len, &w));
+  cudaStream_t s = (cudaStream_t)stream;
+  float* lw = lw_out ? lw_out : w.lw();
+  PPL_TRY(reset_ws(w, false, s));
+  PPL_TRY(cuda_status(cudaMemsetAsync(out_dev, 0, sizeof(ppl_is_result), s)));
+  PPL_TRY(cuda_status(launch_poly_trace(p, data->x, data->y, data->len, n_particles, seed,
+                                        instance, lw, particles_out, w.hdr(), w.partials(),
+                                        out_dev, s)));
+  return PPL_OK;
+}
+
+ppl_status ppl_posterior_finish(const ppl_model* model, const ppl_poly_particle* particles,
+                                const float* lw, int64_t n_particles, uint64_t seed,
+                                uint32_t instance, ppl_is_result* out_dev, void* ws,
+                                size_t ws_bytes, ppl_stream stream) {
+  PolyParams p;
+  PPL_TRY(poly_params(model, &p));
+  if (n_particles < 1 || n_particles > kMaxParticles || !out_dev) return PPL_EINVAL;
+  if (particles && (reinterpret_cast<uintptr_t>(particles) & 15)) return PPL_EINVAL;
+  Ws w;
+  PPL_TRY(check_ws(ws, ws_bytes, n_particles, 0, &w));
+  const float* l = lw ? lw : w.lw();
+  return cuda_status(launch_posterior(p, particles, l, n_particles, seed, instance, w.hdr(),
+                                      w.partials(), out_dev, (cudaStream_t)stream));
+}
+
+ppl_status ppl_infer_is(const ppl_model* model, const ppl_data* data, int64_t n_particles,
+                        uint64_t seed, ppl_is_result* out_dev, float* lw_out,
+                        ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,
+                        ppl_stream stream) {
+  PPL_TRY(ppl_trace_is(model, data, n_particles, seed, 0, out_dev, lw_out, particles_out, ws,
+                       ws_bytes, stream));
+  return ppl_posterior_finish(model, particles_out, lw_out, n_particles, seed, 0, out_dev, ws,
+                              ws_bytes, stream);
+}
+
+ppl_status ppl_infer_is_host(const ppl_model* model, const float* x_host, const float* y_host,
+                             int64_t data_len, int64_t n_particles, uint64_t seed,
+                             ppl_is_result* out_host, void* ws, size_t ws_bytes,
+                             ppl_stream stream) {
+  if (!out_host || data_len < 0 || (data_len > 0 && (!x_host || !y_host))) return PPL_EINVAL;
+  if (n_particles < 1 || n_particles > kMaxParticles) return PPL_EINVAL;
+  Ws w;
+  PPL_TRY(check_ws(ws, ws_bytes, n_particles, data_len, &w));
+  cudaStream_t s = (cudaStream_t)stream;
+  float* xd = reinterpret_cast<float*>(w.scratch());
+  float* yd = xd + data_len;
+  // the summary lands in the scan-prefix region, unused by likelihood weighting
+  ppl_is_result* res = reinterpret_cast<ppl_is_result*>(w.prefix());
+  if (data_len > 0) {
+    PPL_TRY(cuda_status(cudaMemcpyAsync(xd, x_host, data_len * sizeof(float),
+                                        cudaMemcpyHostToDevice, s)));
+    PPL_TRY(cuda_status(cudaMemcpyAsync(yd, y_host, data_len * sizeof(float),
+                                        cudaMemcpyHostToDevice, s)));
+  }
+  ppl_data d{xd, yd, data_len};
+  PPL_TRY(ppl_infer_is(model, &d, n_particles, seed, res, nullptr, nullptr, ws, ws_bytes, stream));
+  PPL_TRY(cuda_status(cudaMemcpyAsync(out_host, res, sizeof(ppl_is_result),
+                                      cudaMemcpyDeviceToHost, s)));
+  PPL_TRY(cuda_status(cudaStreamSynchronize(s)));
+  return (ppl_status)out_host->status;
+}
+
+ppl_status ppl_logsumexp(const float* lw, int64_t n, double* out_dev, void* ws, size_t ws_bytes,
+                         ppl_stream stream) {
+  if (!lw || !out_dev || n < 1 || n > kMaxParticles) return PPL_EINVAL;
+  Ws w;
+  PPL_TRY(check_ws(ws, ws_bytes, n, 0, &w));
+  cudaStream_t s = (cudaStream_t)stream;
+  PPL_TRY(reset_ws(w, false, s));
+  PPL_TRY(cuda_status(launch_stats(lw, nullptr, n, nullptr, w.hdr(), w.partials(), nullptr,
+                                   out_dev, s)));
+  return PPL_OK;
+}
+
+ppl_status ppl_resample(const float* lw, const uint64_t* q_fixed, int64_t n, int64_t m,
+                        uint64_t seed, uint32_t instance, uint32_t t, int32_t* ancestors,
+                        void* ws, size_t ws_bytes, ppl_stream stream) {
+  if ((lw == nullptr) == (q_fixed == nullptr)) return PPL_EINVAL;
+  if (!ancestors || n < 1 || n > kMaxParticles || m < 1 || m > kMaxParticles) return PPL_EINVAL;
+  Ws w;
+  PPL_TRY(check_ws(ws, ws_bytes, n, 0, &w));
+  cudaStream_t s = (cudaStream_t)stream;
+  PPL_TRY(reset_ws(w, true, s));
+  if (lw)
+    PPL_TRY(cuda_status(launch_stats(lw, nullptr, n, nullptr, w.hdr(), w.partials(), nullptr,
+                                     nullptr, s)));
+  PPL_TRY(cuda_status(launch_resample_scan(lw, q_fixed, n, m, seed, instance, t, w.hdr(),
+                                           w.tiles(), w.prefix(), nullptr, s)));
+  PPL_TRY(cuda_status(launch_ancestors(w.prefix(), n, m, w.hdr(), ancestors, nullptr, s)));
+  return PPL_OK;
+}
+
+ppl_status ppl_gather(const void* state_in, int64_t n_in, int64_t stride_bytes,
+                      const int32_t* ancestors, int64_t m, void* state_out, ppl_stream stream) {
+  if (!state_in || !state_out || !ancestors || stride_bytes <= 0 || m < 0 || n_in < 0)
+    return PPL_EINVAL;
+  if (m == 0) return PPL_OK;
+  return cuda_status(launch_gather(state_in, n_in, stride_bytes, ancestors, m, state_out,
+                                   nullptr, (cudaStream_t)stream));
+}
+
+ppl_status ppl_smc_step(const ppl_model* model, float y_t, int32_t t, uint64_t seed, float* x,
+                        float* lw, int64_t n, double* logz_acc, int32_t* resampled,
+                        double* logz_est, void* ws, size_t ws_bytes, ppl_stream stream) {
+  if (!model || model->id != PPL_MODEL_LGSSM) return PPL_EINVAL;
+  if (!(model->obs_sigma > 0.0f) || !isfinite(model->phi) || !isfinite(model->q_sigma))
+    return PPL_EINVAL;
+  if (!x || !lw || !logz_acc || !resampled || !logz_est || t < 1 || n < 1 || n > kMaxParticles)
+    return PPL_EINVAL;
+  Ws w;
+  PPL_TRY(check_ws(ws, ws_bytes, n, 0, &w));
+  cudaStream_t s = (cudaStream_t)stream;
+  const double r2 = (double)model->obs_sigma * (double)model->obs_sigma;
+  LgssmParams p;
+  p.phi = model->phi;
+  p.q_sigma = model->q_sigma;
+  p.obs_const = (float)(-0.5 * log(2.0 * M_PI * r2));
+  p.neg_half_inv_r2 = (float)(-1.0 / (2.0 * r2));
+  int32_t* anc = reinterpret_cast<int32_t*>(w.scratch());
+  float* x_tmp = reinterpret_cast<float*>(w.scratch() + align_up((size_t)n * sizeof(int32_t)));
+  const int32_t* gate = &w.hdr()->resample_flag;
+  PPL_TRY(reset_ws(w, true, s));
+  PPL_TRY(cuda_status(launch_smc_propagate(p, y_t, t, seed, x, lw, n, logz_acc, resampled,
+                                           logz_est, w.hdr(), w.partials(), s)));
+  PPL_TRY(cuda_status(launch_resample_scan(lw, nullptr, n, n, seed, 0, (uint32_t)t, w.hdr(),
+                                           w.tiles(), w.prefix(), gate, s)));
+  PPL_TRY(cuda_status(launch_ancestors(w.prefix(), n, n, w.hdr(), anc, gate, s)));
+  PPL_TRY(cuda_status(launch_gather(x, n, sizeof(float), anc, n, x_tmp, gate, s)));
+  PPL_TRY(cuda_status(launch_smc_commit(x, x_tmp, lw, n, gate, s)));
+  return PPL_OK;
+}
+
+ppl_status ppl_rng_words(uint64_t seed, uint32_t instance, uint32_t step, uint32_t purpose,
+                         int64_t n_particles, int32_t n_blocks, uint32_t* out_dev,
+                         ppl_stream stream) {
+  if (!out_dev || n_particles < 1 || n_particles > kMaxParticles || n_blocks < 1 ||
+      n_blocks > 65535 || purpose > 0xffff)
+    return PPL_EINVAL;
+  if (reinterpret_cast<uintptr_t>(out_dev) & 15) return PPL_EINVAL;
+  return cuda_status(launch_rng_words(seed, instance, step, purpose, n_particles, n_blocks,
+                                      out_dev, (cudaStream_t)stream));
+}
+
+ppl_status ppl_posterior_reduce(const ppl_model* model, const ppl_poly_particle* particles,
+                                const float* lw, int64_t n, ppl_is_result* out_dev, void* ws,
+                                size_t ws_bytes, ppl_stream stream) {
+  PolyParams p;
+  PPL_TRY(poly_params(model, &p));
+  if (!particles || !out_dev || n < 1 || n > kMaxParticles) return PPL_EINVAL;
+  if (reinterpret_cast<uintptr_t>(particles) & 15) return PPL_EINVAL;
+  Ws w;
+  PPL_TRY(check_ws(ws, ws_bytes, n, 0, &w));
+  cudaStream_t s = (cudaStream_t)stream;
+  PPL_TRY(reset_ws(w, false, s));
+  PPL_TRY(cuda_status(cudaMemsetAsync(out_dev, 0, sizeof(ppl_is_result), s)));
+  PPL_TRY(cuda_status(launch_stats(lw, particles, n, &p, w.hdr(), w.partials(), out_dev, nullptr,
+                                   s)));
+  PPL_TRY(cuda_status(
+      launch_posterior(p, particles, lw, n, 0, 0, w.hdr(), w.partials(), out_dev, s)));
+  return PPL_OK;
+}
+
+}  // extern "C"

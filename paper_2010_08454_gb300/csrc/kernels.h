@@ -1,0 +1,63 @@
+// Internal launch interface between the C ABI (abi.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace ppl {
+
+struct PolyParams;
+
+int num_sms();
+int trace_grid(int64_t N);
+int stream_grid(int64_t N);
+size_t partials_bytes();
+
+// is_kernels.cu
+cudaError_t launch_poly_trace(const PolyParams& p, const float* x, const float* y, int64_t L,
+                              int64_t N, uint64_t seed, uint32_t instance, float* lw_out,
+                              ppl_poly_particle* rec_out, WsHeader* hdr, void* parts,
+                              ppl_is_result* res, cudaStream_t s);
+cudaError_t launch_stats(const float* lw, const ppl_poly_particle* rec, int64_t N,
+                         const PolyParams* p, WsHeader* hdr, void* parts, ppl_is_result* res,
+                         double* lse_out, cudaStream_t s);
+cudaError_t launch_posterior(const PolyParams& p, const ppl_poly_particle* rec, const float* lw,
+                             int64_t N, uint64_t seed, uint32_t instance, WsHeader* hdr,
+                             void* parts, ppl_is_result* res, cudaStream_t s);
+
+// resample.cu
+constexpr int kScanItems = 8;
+constexpr int64_t kScanTile = (int64_t)kTpb * kScanItems;
+inline int64_t scan_tiles(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
+// gate: when non-null, the kernels do nothing unless *gate != 0 (SMC steps).
+cudaError_t launch_resample_scan(const float* lw, const uint64_t* q_fixed, int64_t N, int64_t M,
+                                 uint64_t seed, uint32_t instance, uint32_t t, WsHeader* hdr,
+                                 uint64_t* tile_status, uint64_t* prefix, const int32_t* gate,
+                                 cudaStream_t s);
+cudaError_t launch_ancestors(const uint64_t* prefix, int64_t N, int64_t M, const WsHeader* hdr,
+                             int32_t* ancestors, const int32_t* gate, cudaStream_t s);
+cudaError_t launch_gather(const void* in, int64_t n_in, int64_t stride_bytes, const int32_t* anc,
+                          int64_t M, void* out, const int32_t* gate, cudaStream_t s);
+
+// rng_kernels.cu
+cudaError_t launch_rng_words(uint64_t seed, uint32_t instance, uint32_t step, uint32_t purpose,
+                             int64_t n, int32_t n_blocks, uint32_t* out, cudaStream_t s);
+
+// smc.cu
+struct LgssmParams {
+  float phi, q_sigma;
+  float obs_const;      // -log(2 pi r^2) / 2
+  float neg_half_inv_r2;  // -1 / (2 r^2)
+};
+cudaError_t launch_smc_propagate(const LgssmParams& p, float y_t, int32_t t, uint64_t seed,
+                                 float* x, float* lw, int64_t N, double* logz_acc,
+                                 int32_t* resampled, double* logz_est, WsHeader* hdr,
+                                 void* parts, cudaStream_t s);
+cudaError_t launch_smc_commit(float* x, const float* x_tmp, float* lw, int64_t N,
+                              const int32_t* gate, cudaStream_t s);
+
+}  // namespace ppl

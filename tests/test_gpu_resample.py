@@ -1,0 +1,95 @@
+"""Parity of the CUDA normalisation, resampling and gather with the oracle.
+
+Ancestors are compared bit for bit: from identical fixed-point weights, and
+from identical FP32 log-weights (the FP32 exponential that decides the
+integer weights is part of the definition on both sides).
+"""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import load_ppl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ppl():
+    return load_ppl()
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("N,M", [(1, 1), (2, 5), (2047, 2049), (2048, 2048), (2049, 100),
+                                 (100003, 77777), (65536, 300000)])
+def test_fixed_point_ancestors_bit_exact(ppl, orc, N, M):
+    q = synth.fixed_weights(N, N + M)
+    if q.sum() == 0:
+        q[0] = 3
+    anc = ppl.ppl_resample(M, 5, instance=2, t=9, q_fixed=_t(q.view(np.int64))).cpu().numpy()
+    st, ref = orc.resample_systematic(q, M, 5, 2, 9)
+    assert st == 0 and np.array_equal(anc, ref)
+
+
+@pytest.mark.parametrize("kind", ["normal", "equal", "onehot", "sparse", "wide"])
+@pytest.mark.parametrize("N", [1, 777, 4099, 262147])
+def test_log_weight_ancestors_bit_exact(ppl, orc, kind, N):
+    lw = synth.log_weights(N, 3 + N, kind)
+    anc = ppl.ppl_resample(N, 11, t=4, lw=_t(lw)).cpu().numpy()
+    st, ref = orc.resample_from_lw(lw, N, 11, 0, 4)
+    assert st == 0 and np.array_equal(anc, ref)
+
+
+@pytest.mark.parametrize("kind", ["normal", "onehot"])
+def test_full_size_2_24(ppl, orc, kind):
+    N = 1 << 24
+    lw = synth.log_weights(N, 12, kind, scale=30.0)
+    anc = ppl.ppl_resample(N, 1, t=0, lw=_t(lw)).cpu().numpy()
+    st, ref = orc.resample_from_lw(lw, N, 1, 0, 0)
+    assert st == 0 and np.array_equal(anc, ref)
+
+
+def test_gather_records(ppl, orc):
+    rng = np.random.default_rng(2)
+    for rec_shape, dtype in [((5000, 8), np.float32), ((3001,), np.float32),
+                             ((1234, 3), np.int16)]:
+        rec = rng.integers(-1000, 1000, rec_shape).astype(dtype)
+        anc = np.sort(rng.integers(0, rec_shape[0], 4321)).astype(np.int32)
+        out = ppl.ppl_gather(_t(rec), _t(anc)).cpu().numpy()
+        assert np.array_equal(out, orc.gather(rec, anc))
+    # an ancestor out of range gives a zero record, never a stray read
+    rec = np.arange(40, dtype=np.float32).reshape(5, 8)
+    out = ppl.ppl_gather(_t(rec), _t(np.array([0, 7, -1, 4], dtype=np.int32))).cpu().numpy()
+    assert np.array_equal(out[0], rec[0]) and np.array_equal(out[3], rec[4])
+    assert np.all(out[1] == 0) and np.all(out[2] == 0)
+
+
+@pytest.mark.parametrize("N", [1, 100, 100003, 1 << 24])
+def test_logsumexp(ppl, orc, N):
+    lw = synth.log_weights(N, 4, "normal", scale=20.0)
+    out = ppl.ppl_logsumexp(_t(lw)).cpu().numpy()
+    ref = orc.lse_ess(lw.astype(np.float64))
+    assert out[0] == pytest.approx(ref["lse"], abs=1e-5)
+    assert out[1] == pytest.approx(ref["ess"], rel=1e-5)
+    assert out[2] == ref["max_lw"] and int(out[3]) == ref["argmax"]
+
+
+def test_device_errors_are_reported(ppl):
+    import torch
+    lw = np.zeros(5000, dtype=np.float32)
+    lw[1234] = np.nan
+    ws = ppl.workspace(ppl.poly_model(), 5000)
+    ppl.ppl_logsumexp(_t(lw), ws=ws)
+    assert ppl.ppl_workspace_status(ws) == ppl.PPL_ENAN
+    ppl.ppl_logsumexp(_t(np.full(5000, -np.inf, dtype=np.float32)), ws=ws)
+    assert ppl.ppl_workspace_status(ws) == ppl.PPL_EEMPTY
+    ppl.ppl_resample(5000, 0, q_fixed=_t(np.full(5000, 1 << 60, dtype=np.int64)), ws=ws)
+    assert ppl.ppl_workspace_status(ws) == ppl.PPL_EINVAL
+    ppl.ppl_resample(5000, 0, q_fixed=_t(np.zeros(5000, dtype=np.int64)), ws=ws)
+    assert ppl.ppl_workspace_status(ws) == ppl.PPL_EEMPTY
+    ppl.ppl_resample(5000, 0, lw=_t(np.zeros(5000, dtype=np.float32)), ws=ws)
+    assert ppl.ppl_workspace_status(ws) == ppl.PPL_OK
+    torch.cuda.synchronize()
