@@ -200,6 +200,23 @@ ppl_status ppl_rng_words(uint64_t seed, uint32_t instance, uint32_t step, uint32
                          int64_t n_particles, int32_t n_blocks, uint32_t* out_dev,
                          ppl_stream stream);
 
+/* ppl_resample without a workspace, for callers that cannot allocate device
+ * memory: a plugin whose host application owns every device allocation
+ * through its own pool, or a real-time loop that must not risk the implicit
+ * device synchronisation of cudaMalloc.  The paper has no counterpart; this is
+ * a library convenience.  Same arguments and result as ppl_resample, but the
+ * scratch is a static device array of about 9.3 MB per device, so n must be at
+ * most 2^20 (1048576) particles; larger n returns PPL_EINVAL.  Nothing is
+ * allocated.  The first call on a device looks the array's address up and
+ * caches it (make that first call before any stream capture).  All calls on a
+ * device share the array: calls whose work overlaps on the GPU race, so issue
+ * them in one stream.  Device-side errors are read with
+ * ppl_resample_noalloc_status, which synchronises `stream`. */
+ppl_status ppl_resample_noalloc(const float* lw, const uint64_t* q_fixed, int64_t n, int64_t m,
+                                uint64_t seed, uint32_t instance, uint32_t t, int32_t* ancestors,
+                                ppl_stream stream);
+ppl_status ppl_resample_noalloc_status(ppl_stream stream);
+
 #ifdef __cplusplus
 }
 #endif
