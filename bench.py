@@ -38,7 +38,7 @@ UNIT = "traces/s"
 WORKLOAD = ("linefitting likelihood weighting, 2^24 particles x 256 points, degree "
             "uniform{2..5}, coefficients N(0,10^2), sigma 0.5; + log-sum-exp/ESS + posterior "
             "reduce + systematic resampling (64-bit fixed point) + gather of 32-byte records")
-KERNELS_PER_STEP = 6  # trace, posterior, max/LSE pass, scan, ancestors, gather
+KERNELS_PER_STEP = 5  # trace (posterior fused), max/LSE pass, scan, ancestors, gather
 
 
 def parse():
@@ -241,12 +241,10 @@ def run_ours(args):
     def step(ev=None):
         if ev:
             ev[0].record(stream)
-        ppl.ppl_trace_is(model, xd, yd, N, INFER_SEED, instance, out=res, lw_out=lw,
-                         particles_out=parts, ws=ws)
+        ppl.ppl_infer_is_instance(model, xd, yd, N, INFER_SEED, instance, out=res, lw_out=lw,
+                                  particles_out=parts, ws=ws)
         if ev:
             ev[1].record(stream)
-        ppl.ppl_posterior_finish(model, N, INFER_SEED, res, ws, instance, particles=parts, lw=lw)
-        if ev:
             ev[2].record(stream)
         ppl.ppl_resample(N, INFER_SEED, instance, 0, lw=lw, ancestors=anc, ws=ws)
         if ev:
@@ -306,8 +304,8 @@ def run_ours(args):
     for _ in range(n_e2e):
         xd.copy_(xh, non_blocking=True)
         yd.copy_(yh, non_blocking=True)
-        ppl.ppl_infer_is(model, xd, yd, N, INFER_SEED, out=res, lw_out=lw, particles_out=parts,
-                         ws=ws)
+        ppl.ppl_infer_is_instance(model, xd, yd, N, INFER_SEED, instance, out=res, lw_out=lw,
+                                  particles_out=parts, ws=ws)
         ppl.ppl_resample(N, INFER_SEED, instance, 0, lw=lw, ancestors=anc, ws=ws)
         ppl.ppl_gather(parts, anc, state_out=parts_out)
         res_h.copy_(res, non_blocking=True)

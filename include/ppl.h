@@ -123,22 +123,15 @@ ppl_status ppl_infer_is(const ppl_model* model, const ppl_data* data, int64_t n_
                         ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,
                         ppl_stream stream);
 
-/* The two stages ppl_infer_is runs, for callers that time or skip them.
- * ppl_trace_is: the traces of instance `instance` (counter field) with the
- * normalisation fused in; fills log_z, lse, ess, max_lw, argmax and the
- * per-degree bests of *out_dev and leaves the statistics in `ws`.
- * ppl_posterior_finish: the posterior pass (p_n, mean_c, deg_mean, deg_var,
- * map_deg) over the same population, using the statistics a ppl_trace_is on
- * the same `ws` left; particles NULL regenerates the draws from their counters,
- * lw NULL reads the log-weights ppl_trace_is kept in `ws`. */
-ppl_status ppl_trace_is(const ppl_model* model, const ppl_data* data, int64_t n_particles,
-                        uint64_t seed, uint32_t instance, ppl_is_result* out_dev, float* lw_out,
-                        ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,
-                        ppl_stream stream);
-ppl_status ppl_posterior_finish(const ppl_model* model, const ppl_poly_particle* particles,
-                                const float* lw, int64_t n_particles, uint64_t seed,
-                                uint32_t instance, ppl_is_result* out_dev, void* ws,
-                                size_t ws_bytes, ppl_stream stream);
+/* ppl_infer_is for instance `instance` of a batch: the counter field
+ * `instance` of every draw is set to it, so independent instances (or ranks)
+ * with one seed draw independent traces.  ppl_infer_is uses instance 0.  The
+ * whole summary (normalisation and posterior) comes out of one fused kernel. */
+ppl_status ppl_infer_is_instance(const ppl_model* model, const ppl_data* data,
+                                 int64_t n_particles, uint64_t seed, uint32_t instance,
+                                 ppl_is_result* out_dev, float* lw_out,
+                                 ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,
+                                 ppl_stream stream);
 
 /* Same as ppl_infer_is with the data and the result in host memory: copies x,
  * y in, runs, copies the summary out, and synchronises `stream` before it
@@ -199,6 +192,46 @@ ppl_status ppl_posterior_reduce(const ppl_model* model, const ppl_poly_particle*
 ppl_status ppl_rng_words(uint64_t seed, uint32_t instance, uint32_t step, uint32_t purpose,
                          int64_t n_particles, int32_t n_blocks, uint32_t* out_dev,
                          ppl_stream stream);
+
+/* Batched likelihood weighting: many independent line-fitting data sets of
+ * uneven size in one persistent launch.  Instance b has data x, y [dev] at
+ * [data_off[b], data_off[b+1]) and part_off[b+1] - part_off[b] >= 1 particles;
+ * its draws use counter field instance = b.  The work is cut into (instance,
+ * tile of 256 * ppt particles) items taken heaviest first (longest data first)
+ * from an atomic queue by num_SMs * blocks_per_sm resident blocks; the last
+ * item of an instance writes out_dev[b] [dev].
+ *  ppl_batched_workspace_size: bytes for any configuration (host offsets).
+ *  ppl_batched_prepare: builds the item plan on the host from host copies of
+ *    the offsets, copies it into `ws` and synchronises `stream`; fills *plan.
+ *  ppl_infer_is_batched: the launch (a memset, a device copy and one kernel);
+ *    it can be captured in a CUDA graph and replayed.
+ *  ppl_batched_autotune: times every ppt in {1,2,4,8} x blocks_per_sm in
+ *    {1..4} on the caller's data, keeps the fastest (cached as one JSON line in
+ *    cache_path, reused when the batch's shape matches), and prepares it. */
+typedef struct {
+  int32_t ppt, blocks_per_sm, n_inst, pad;
+  int64_t n_items, max_len, total_particles;
+  double work; /* sum over instances of particles x data points */
+} ppl_batch_plan;
+
+size_t ppl_batched_workspace_size(const int64_t* data_off_host, const int64_t* part_off_host,
+                                  int32_t n_inst, int32_t ppt);
+ppl_status ppl_batched_prepare(const ppl_model* model, const int64_t* data_off_host,
+                               const int64_t* part_off_host, int32_t n_inst, int32_t ppt,
+                               int32_t blocks_per_sm, ppl_batch_plan* plan, void* ws,
+                               size_t ws_bytes, ppl_stream stream);
+ppl_status ppl_infer_is_batched(const ppl_model* model, const float* x, const float* y,
+                                const int64_t* data_off, const int64_t* part_off,
+                                int32_t n_inst, uint64_t seed, const ppl_batch_plan* plan,
+                                ppl_is_result* out_dev, void* ws, size_t ws_bytes,
+                                ppl_stream stream);
+ppl_status ppl_batched_autotune(const ppl_model* model, const float* x, const float* y,
+                                const int64_t* data_off_dev, const int64_t* part_off_dev,
+                                const int64_t* data_off_host, const int64_t* part_off_host,
+                                int32_t n_inst, uint64_t seed, ppl_is_result* out_dev, void* ws,
+                                size_t ws_bytes, const char* cache_path, ppl_batch_plan* best,
+                                ppl_stream stream);
+ppl_status ppl_batched_status(const void* ws, ppl_stream stream);
 
 /* ppl_resample without a workspace, for callers that cannot allocate device
  * memory: a plugin whose host application owns every device allocation

@@ -62,6 +62,13 @@ class PplIsResult(ctypes.Structure):
 
 RESULT_BYTES = ctypes.sizeof(PplIsResult)
 
+
+class PplBatchPlan(ctypes.Structure):
+    _fields_ = [("ppt", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
+                ("n_inst", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("n_items", ctypes.c_int64), ("max_len", ctypes.c_int64),
+                ("total_particles", ctypes.c_int64), ("work", ctypes.c_double)]
+
 _SIGS = {
     "ppl_status_string": (ctypes.c_char_p, [ctypes.c_int32]),
     "ppl_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]),
@@ -70,14 +77,10 @@ _SIGS = {
                                     ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                     ctypes.c_void_p]),
-    "ppl_trace_is": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
-                                    ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
-                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                    ctypes.c_size_t, ctypes.c_void_p]),
-    "ppl_posterior_finish": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                            ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
-                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
-                                            ctypes.c_void_p]),
+    "ppl_infer_is_instance": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                             ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_size_t, ctypes.c_void_p]),
     "ppl_infer_is_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
@@ -103,6 +106,22 @@ _SIGS = {
                                             ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
                                             ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p]),
     "ppl_resample_noalloc_status": (ctypes.c_int, [ctypes.c_void_p]),
+    "ppl_batched_workspace_size": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_void_p,
+                                                     ctypes.c_int32, ctypes.c_int32]),
+    "ppl_batched_prepare": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                           ctypes.c_void_p]),
+    "ppl_infer_is_batched": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                            ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "ppl_batched_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint64,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                            ctypes.c_char_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "ppl_batched_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "ppl_posterior_reduce": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_size_t, ctypes.c_void_p]),
@@ -206,9 +225,9 @@ def ppl_infer_is(model, x, y, n_particles, seed, out=None, lw_out=None, particle
     return out
 
 
-def ppl_trace_is(model, x, y, n_particles, seed, instance=0, out=None, lw_out=None,
-                 particles_out=None, ws=None, stream=None):
-    """Traces + fused normalisation (first stage of ppl_infer_is)."""
+def ppl_infer_is_instance(model, x, y, n_particles, seed, instance, out=None, lw_out=None,
+                          particles_out=None, ws=None, stream=None):
+    """ppl_infer_is with the counter field `instance` set (independent instances)."""
     _dev_f32(x, "x")
     _dev_f32(y, "y")
     if ws is None:
@@ -216,20 +235,11 @@ def ppl_trace_is(model, x, y, n_particles, seed, instance=0, out=None, lw_out=No
     if out is None:
         out = result_tensor(x.device)
     data = PplData(x.data_ptr(), y.data_ptr(), x.numel())
-    st = lib().ppl_trace_is(ctypes.byref(model), ctypes.byref(data), int(n_particles),
-                            ctypes.c_uint64(seed), int(instance), _ptr(out), _ptr(lw_out),
-                            _ptr(particles_out), _ptr(ws), ws.numel(), _stream(stream))
-    _check(st, "ppl_trace_is")
-    return out
-
-
-def ppl_posterior_finish(model, n_particles, seed, out, ws, instance=0, particles=None,
-                         lw=None, stream=None):
-    """Posterior pass after ppl_trace_is on the same workspace (second stage)."""
-    st = lib().ppl_posterior_finish(ctypes.byref(model), _ptr(particles), _ptr(lw),
-                                    int(n_particles), ctypes.c_uint64(seed), int(instance),
-                                    _ptr(out), _ptr(ws), ws.numel(), _stream(stream))
-    _check(st, "ppl_posterior_finish")
+    st = lib().ppl_infer_is_instance(ctypes.byref(model), ctypes.byref(data), int(n_particles),
+                                     ctypes.c_uint64(seed), int(instance), _ptr(out),
+                                     _ptr(lw_out), _ptr(particles_out), _ptr(ws), ws.numel(),
+                                     _stream(stream))
+    _check(st, "ppl_infer_is_instance")
     return out
 
 
@@ -335,3 +345,70 @@ def decode_particles(p):
     deg = p[:, 6].contiguous().view(torch.int32)
     origin = p[:, 7].contiguous().view(torch.int32).to(torch.int64) & 0xFFFFFFFF
     return c, deg, origin
+
+
+# ---- batched likelihood weighting ---------------------------------------
+def _host_i64(a):
+    a = np.ascontiguousarray(a, dtype=np.int64)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def ppl_batched_workspace_size(data_off, part_off, ppt=1):
+    d, dp = _host_i64(data_off)
+    p, pp = _host_i64(part_off)
+    return int(lib().ppl_batched_workspace_size(dp, pp, len(d) - 1, int(ppt)))
+
+
+def batched_workspace(data_off, part_off, device="cuda"):
+    n = ppl_batched_workspace_size(data_off, part_off, 1)
+    if n == 0:
+        raise ValueError("invalid batch offsets")
+    return torch.empty(n, dtype=torch.uint8, device=device)
+
+
+def ppl_batched_prepare(model, data_off, part_off, ppt, blocks_per_sm, ws, stream=None):
+    d, dp = _host_i64(data_off)
+    p, pp = _host_i64(part_off)
+    plan = PplBatchPlan()
+    st = lib().ppl_batched_prepare(ctypes.byref(model), dp, pp, len(d) - 1, int(ppt),
+                                   int(blocks_per_sm), ctypes.byref(plan), _ptr(ws), ws.numel(),
+                                   _stream(stream))
+    _check(st, "ppl_batched_prepare")
+    return plan
+
+
+def ppl_infer_is_batched(model, x, y, data_off, part_off, seed, plan, out, ws, stream=None):
+    """Launch on device tensors x, y (float32) and data_off, part_off (int64)."""
+    st = lib().ppl_infer_is_batched(ctypes.byref(model), _ptr(x), _ptr(y), _ptr(data_off),
+                                    _ptr(part_off), plan.n_inst, ctypes.c_uint64(seed),
+                                    ctypes.byref(plan), _ptr(out), _ptr(ws), ws.numel(),
+                                    _stream(stream))
+    _check(st, "ppl_infer_is_batched")
+    return out
+
+
+def ppl_batched_autotune(model, x, y, data_off, part_off, data_off_host, part_off_host, seed,
+                         out, ws, cache_path=None, stream=None):
+    d, dp = _host_i64(data_off_host)
+    p, pp = _host_i64(part_off_host)
+    plan = PplBatchPlan()
+    st = lib().ppl_batched_autotune(ctypes.byref(model), _ptr(x), _ptr(y), _ptr(data_off),
+                                    _ptr(part_off), dp, pp, len(d) - 1, ctypes.c_uint64(seed),
+                                    _ptr(out), _ptr(ws), ws.numel(),
+                                    cache_path.encode() if cache_path else None,
+                                    ctypes.byref(plan), _stream(stream))
+    _check(st, "ppl_batched_autotune")
+    return plan
+
+
+def ppl_batched_status(ws, stream=None):
+    return int(lib().ppl_batched_status(_ptr(ws), _stream(stream)))
+
+
+def batch_results_tensor(n_inst, device="cuda"):
+    return torch.zeros(n_inst * RESULT_BYTES, dtype=torch.uint8, device=device)
+
+
+def read_batch_results(out, n_inst):
+    raw = out.detach().cpu().numpy().tobytes()
+    return [PplIsResult.from_buffer_copy(raw, i * RESULT_BYTES).as_dict() for i in range(n_inst)]

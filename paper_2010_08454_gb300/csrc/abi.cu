@@ -124,10 +124,11 @@ ppl_status ppl_workspace_status(const void* ws, ppl_stream stream) {
   return (ppl_status)st;
 }
 
-ppl_status ppl_trace_is(const ppl_model* model, const ppl_data* data, int64_t n_particles,
-                        uint64_t seed, uint32_t instance, ppl_is_result* out_dev, float* lw_out,
-                        ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,
-                        ppl_stream stream) {
+ppl_status ppl_infer_is_instance(const ppl_model* model, const ppl_data* data,
+                                 int64_t n_particles, uint64_t seed, uint32_t instance,
+                                 ppl_is_result* out_dev, float* lw_out,
+                                 ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,
+                                 ppl_stream stream) {
   PolyParams p;
   PPL_TRY(poly_params(model, &p));
   if (!data || data->len < 0 || (data->len > 0 && (!data->x || !data->y))) return PPL_EINVAL;
@@ -136,38 +137,20 @@ ppl_status ppl_trace_is(const ppl_model* model, const ppl_data* data, int64_t n_
   Ws w;
   PPL_TRY(check_ws(ws, ws_bytes, n_particles, data->len, &w));
   cudaStream_t s = (cudaStream_t)stream;
-  float* lw = lw_out ? lw_out : w.lw();
   PPL_TRY(reset_ws(w, false, s));
   PPL_TRY(cuda_status(cudaMemsetAsync(out_dev, 0, sizeof(ppl_is_result), s)));
   PPL_TRY(cuda_status(launch_poly_trace(p, data->x, data->y, data->len, n_particles, seed,
-                                        instance, lw, particles_out, w.hdr(), w.partials(),
+                                        instance, lw_out, particles_out, w.hdr(), w.partials(),
                                         out_dev, s)));
   return PPL_OK;
-}
-
-ppl_status ppl_posterior_finish(const ppl_model* model, const ppl_poly_particle* particles,
-                                const float* lw, int64_t n_particles, uint64_t seed,
-                                uint32_t instance, ppl_is_result* out_dev, void* ws,
-                                size_t ws_bytes, ppl_stream stream) {
-  PolyParams p;
-  PPL_TRY(poly_params(model, &p));
-  if (n_particles < 1 || n_particles > kMaxParticles || !out_dev) return PPL_EINVAL;
-  if (particles && (reinterpret_cast<uintptr_t>(particles) & 15)) return PPL_EINVAL;
-  Ws w;
-  PPL_TRY(check_ws(ws, ws_bytes, n_particles, 0, &w));
-  const float* l = lw ? lw : w.lw();
-  return cuda_status(launch_posterior(p, particles, l, n_particles, seed, instance, w.hdr(),
-                                      w.partials(), out_dev, (cudaStream_t)stream));
 }
 
 ppl_status ppl_infer_is(const ppl_model* model, const ppl_data* data, int64_t n_particles,
                         uint64_t seed, ppl_is_result* out_dev, float* lw_out,
                         ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,
                         ppl_stream stream) {
-  PPL_TRY(ppl_trace_is(model, data, n_particles, seed, 0, out_dev, lw_out, particles_out, ws,
-                       ws_bytes, stream));
-  return ppl_posterior_finish(model, particles_out, lw_out, n_particles, seed, 0, out_dev, ws,
-                              ws_bytes, stream);
+  return ppl_infer_is_instance(model, data, n_particles, seed, 0, out_dev, lw_out,
+                               particles_out, ws, ws_bytes, stream);
 }
 
 ppl_status ppl_infer_is_host(const ppl_model* model, const float* x_host, const float* y_host,
@@ -204,8 +187,7 @@ ppl_status ppl_logsumexp(const float* lw, int64_t n, double* out_dev, void* ws, 
   PPL_TRY(check_ws(ws, ws_bytes, n, 0, &w));
   cudaStream_t s = (cudaStream_t)stream;
   PPL_TRY(reset_ws(w, false, s));
-  PPL_TRY(cuda_status(launch_stats(lw, nullptr, n, nullptr, w.hdr(), w.partials(), nullptr,
-                                   out_dev, s)));
+  PPL_TRY(cuda_status(launch_stats(lw, n, w.hdr(), w.partials(), out_dev, s)));
   return PPL_OK;
 }
 
@@ -219,8 +201,7 @@ ppl_status ppl_resample(const float* lw, const uint64_t* q_fixed, int64_t n, int
   cudaStream_t s = (cudaStream_t)stream;
   PPL_TRY(reset_ws(w, true, s));
   if (lw)
-    PPL_TRY(cuda_status(launch_stats(lw, nullptr, n, nullptr, w.hdr(), w.partials(), nullptr,
-                                     nullptr, s)));
+    PPL_TRY(cuda_status(launch_stats(lw, n, w.hdr(), w.partials(), nullptr, s)));
   PPL_TRY(cuda_status(launch_resample_scan(lw, q_fixed, n, m, seed, instance, t, w.hdr(),
                                            w.tiles(), w.prefix(), nullptr, s)));
   PPL_TRY(cuda_status(launch_ancestors(w.prefix(), n, m, w.hdr(), ancestors, nullptr, s)));
@@ -290,10 +271,7 @@ ppl_status ppl_posterior_reduce(const ppl_model* model, const ppl_poly_particle*
   cudaStream_t s = (cudaStream_t)stream;
   PPL_TRY(reset_ws(w, false, s));
   PPL_TRY(cuda_status(cudaMemsetAsync(out_dev, 0, sizeof(ppl_is_result), s)));
-  PPL_TRY(cuda_status(launch_stats(lw, particles, n, &p, w.hdr(), w.partials(), out_dev, nullptr,
-                                   s)));
-  PPL_TRY(cuda_status(
-      launch_posterior(p, particles, lw, n, 0, 0, w.hdr(), w.partials(), out_dev, s)));
+  PPL_TRY(cuda_status(launch_posterior(p, particles, lw, n, w.hdr(), w.partials(), out_dev, s)));
   return PPL_OK;
 }
 

@@ -1,295 +1,180 @@
 // Likelihood weighting on the line-fitting model: the trace kernel (§3.6.2 run
-// the model N times; Fig. 1 the model), the statistics pass (log-sum-exp
-// normalisation and ESS), and the posterior pass (degree masses, weighted
-// coefficient means and variances, the mode).
+// the model N times and normalise the log-weights; Fig. 1 the model) with the
+// posterior reduction fused in (degree masses, weighted coefficient means and
+// variances, the mode), the statistics pass over given log-weights, and the
+// one-pass posterior summary of a given population.
 #include "kernels.h"
 #include "poly.cuh"
+#include "posterior.cuh"
 #include "stats.cuh"
+#include "trace.cuh"
 
 namespace ppl {
 
 // ---------------------------------------------------------------------------
-// Trace kernel: every thread runs PPT traces per group; the data set streams
-// through shared memory in chunks; the log-weight is the factor
-// -sum_l (y_l - f(x_l))^2 / (2 sigma^2) with f evaluated by Horner's rule in
-// FP32 FMAs.  The statistics pass is fused: each block leaves a partial and
-// the last block merges them.
+// Final merge of the per-block partials, by the last block: warp k merges
+// degree k's partials (FP32, a lane-strided chain then a shuffle tree); the
+// sums S, S2 are recombined in FP64 around the merged maximum; thread 0
+// writes the summary.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void kahan_add(float& sum, float& comp, float v) {
-  const float y = __fsub_rn(v, comp);
-  const float t = __fadd_rn(sum, y);
-  comp = __fsub_rn(__fsub_rn(t, sum), y);
-  sum = t;
+__device__ __forceinline__ void finalize_partials(const DegPartial* parts, int G, int n_deg,
+                                                  int min_deg, int64_t N, WsHeader* hdr,
+                                                  ppl_is_result* res) {
+  __shared__ DegPartial fin[kMaxDegrees];
+  __shared__ double fS[kMaxDegrees], fS2[kMaxDegrees];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp < kMaxDegrees) {
+    DegPartial a;
+    deg_empty(a);
+    for (int b = lane; b < G; b += 32) deg_merge(a, parts[b * kMaxDegrees + warp]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const DegPartial other = deg_shfl_xor(a, o);
+      deg_merge(a, other);
+    }
+    const float M = a.m;
+    double s = 0.0, s2 = 0.0;
+    if (M != -INFINITY) {
+      for (int b = lane; b < G; b += 32) {
+        const DegPartial& q = parts[b * kMaxDegrees + warp];
+        if (q.m == -INFINITY) continue;
+        const double e = (double)expf(q.m - M);
+        s += (double)q.S * e;
+        s2 += (double)q.S2 * e * e;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+      fin[warp] = a;
+      fS[warp] = s;
+      fS2[warp] = s2;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool any = false;
+    for (int k = 0; k < n_deg; ++k) any |= fin[k].m != -INFINITY;
+    if (!any) record_status(&hdr->status, PPL_EEMPTY);
+    if (res) write_summary(fin, fS, fS2, n_deg, min_deg, N, ld_volatile_i32(&hdr->status), res);
+  }
 }
 
+// ---------------------------------------------------------------------------
+// Trace kernel: a persistent grid; each block runs groups of kTpb * PPT traces
+// (trace_group: draw, sort by degree, degree-specialised Horner, per-degree
+// partials) and merges the groups' partials into its running partial; the
+// last block merges the blocks' partials into the summary.
+// ---------------------------------------------------------------------------
 template <int PPT>
 __global__ void __launch_bounds__(kTpb) poly_trace_kernel(
     PolyParams p, const float* __restrict__ xs, const float* __restrict__ ys, int64_t L,
     int64_t N, uint64_t seed, uint32_t instance, int chunk, float* __restrict__ lw_out,
-    ppl_poly_particle* __restrict__ rec_out, WsHeader* hdr, StatPartial* parts,
+    ppl_poly_particle* __restrict__ rec_out, WsHeader* hdr, DegPartial* parts,
     ppl_is_result* res) {
-  extern __shared__ float2 sdata[];
+  extern __shared__ __align__(16) unsigned char smem[];
+  TraceSmem<PPT>& ts = *reinterpret_cast<TraceSmem<PPT>*>(smem);
+  float2* sdata = reinterpret_cast<float2*>(smem + trace_smem_bytes<PPT>());
+  __shared__ DegPartial run[kMaxDegrees], gout[kMaxDegrees];
+  const int tid = threadIdx.x;
   const int64_t group = (int64_t)kTpb * PPT;
   const int64_t n_groups = (N + group - 1) / group;
-  const int n_chunks = (int)((L + chunk - 1) / chunk);
-  const int tid = threadIdx.x;
-
-  if (n_chunks == 1) {
+  const bool resident = L <= chunk;
+  if (tid < kMaxDegrees) deg_empty(run[tid]);
+  if (resident)
     for (int l = tid; l < L; l += kTpb) sdata[l] = make_float2(xs[l], ys[l]);
-    __syncthreads();
-  }
-
-  StatAcc acc;
-  acc.init();
+  __syncthreads();
+  int nan = 0;
   for (int64_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
-    float c[PPT][kMaxCoef];
-    float ss[PPT], comp[PPT];  // compensated (Kahan) sum of the 16-point partial sums
-    int n[PPT];
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-      const int64_t i = g * group + (int64_t)q * kTpb + tid;
-      n[q] = poly_draw(p, seed, instance, (uint32_t)(i < N ? i : 0), c[q]);
-      ss[q] = 0.0f;
-      comp[q] = 0.0f;
-    }
-    for (int ch = 0; ch < n_chunks; ++ch) {
-      const int64_t l0 = (int64_t)ch * chunk;
-      const int len = (int)(L - l0 < (int64_t)chunk ? L - l0 : (int64_t)chunk);
-      if (n_chunks > 1) {
-        __syncthreads();
-        for (int l = tid; l < len; l += kTpb) sdata[l] = make_float2(xs[l0 + l], ys[l0 + l]);
-        __syncthreads();
-      }
-      // Inner sums over 16 points keep the FP32 accumulation error small.
-      int l = 0;
-      for (; l + 16 <= len; l += 16) {
-        float part[PPT];
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) part[q] = 0.0f;
-#pragma unroll 4
-        for (int j = 0; j < 16; ++j) {
-          const float2 d = sdata[l + j];
-#pragma unroll
-          for (int q = 0; q < PPT; ++q) {
-            float f = c[q][5];
-            f = fmaf(f, d.x, c[q][4]);
-            f = fmaf(f, d.x, c[q][3]);
-            f = fmaf(f, d.x, c[q][2]);
-            f = fmaf(f, d.x, c[q][1]);
-            f = fmaf(f, d.x, c[q][0]);
-            const float r = d.y - f;
-            part[q] = fmaf(r, r, part[q]);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) kahan_add(ss[q], comp[q], part[q]);
-      }
-      if (l < len) {
-        float part[PPT];
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) part[q] = 0.0f;
-        for (; l < len; ++l) {
-          const float2 d = sdata[l];
-#pragma unroll
-          for (int q = 0; q < PPT; ++q) {
-            float f = c[q][5];
-            f = fmaf(f, d.x, c[q][4]);
-            f = fmaf(f, d.x, c[q][3]);
-            f = fmaf(f, d.x, c[q][2]);
-            f = fmaf(f, d.x, c[q][1]);
-            f = fmaf(f, d.x, c[q][0]);
-            const float r = d.y - f;
-            part[q] = fmaf(r, r, part[q]);
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < PPT; ++q) kahan_add(ss[q], comp[q], part[q]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) {
-      const int64_t i = g * group + (int64_t)q * kTpb + tid;
-      if (i < N) {
-        const float lw = ss[q] * p.neg_half_inv_var;
-        if (lw_out) lw_out[i] = lw;
-        if (rec_out) {
-          float4* dst = reinterpret_cast<float4*>(rec_out + i);
-          dst[0] = make_float4(c[q][0], c[q][1], c[q][2], c[q][3]);
-          dst[1] = make_float4(c[q][4], c[q][5], __int_as_float(n[q]),
-                               __uint_as_float((uint32_t)i));
-        }
-        acc.add(lw, (int)i, n[q] - p.min_deg);
-      }
-    }
+    trace_group<PPT>(p, xs, ys, L, chunk, resident, sdata, N, g * group, seed, instance, lw_out,
+                     rec_out, ts, gout);
+    if (tid < kMaxDegrees) deg_merge(run[tid], gout[tid]);
+    if (tid == 0) nan |= ts.nan;
   }
-
-  StatAcc r = block_reduce_stat(acc);
-  if (tid == 0) to_partial(r, parts + blockIdx.x);
-  if (elect_last_block(&hdr->ticket[0])) finalize_stats(parts, gridDim.x, N, &p, hdr, res, nullptr);
+  __syncthreads();
+  if (tid < kMaxDegrees) parts[blockIdx.x * kMaxDegrees + tid] = run[tid];
+  if (tid == 0 && nan) record_status(&hdr->status, PPL_ENAN);
+  if (elect_last_block(&hdr->ticket[0]))
+    finalize_partials(parts, gridDim.x, p.n_deg, p.min_deg, N, hdr, res);
 }
 
 // ---------------------------------------------------------------------------
-// Statistics pass over an existing population: lw (NULL = all 0) and, for the
-// per-degree bests, the particles' degrees (NULL = no degrees).
+// Statistics pass over an existing set of log-weights (lw NULL = all 0).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTpb) stats_kernel(const float* __restrict__ lw,
-                                                     const ppl_poly_particle* __restrict__ rec,
-                                                     int64_t N, PolyParams p, int has_model,
+__global__ void __launch_bounds__(kTpb) stats_kernel(const float* __restrict__ lw, int64_t N,
                                                      WsHeader* hdr, StatPartial* parts,
-                                                     ppl_is_result* res, double* lse_out) {
+                                                     double* lse_out) {
   StatAcc acc;
   acc.init();
   const int64_t stride = (int64_t)gridDim.x * kTpb;
-  for (int64_t i = (int64_t)blockIdx.x * kTpb + threadIdx.x; i < N; i += stride) {
-    const float v = lw ? lw[i] : 0.0f;
-    const int d = rec ? rec[i].n - p.min_deg : -1;
-    acc.add(v, (int)i, d);
-  }
+  for (int64_t i = (int64_t)blockIdx.x * kTpb + threadIdx.x; i < N; i += stride)
+    acc.add(lw ? lw[i] : 0.0f, (int)i, -1);
   StatAcc r = block_reduce_stat(acc);
   if (threadIdx.x == 0) to_partial(r, parts + blockIdx.x);
   if (elect_last_block(&hdr->ticket[0]))
-    finalize_stats(parts, gridDim.x, N, has_model ? &p : nullptr, hdr, res, lse_out);
+    finalize_stats(parts, gridDim.x, N, nullptr, hdr, nullptr, lse_out);
 }
 
 // ---------------------------------------------------------------------------
-// Posterior pass: per-degree weighted sums around each degree's best trace,
-// then the summary.  FROM_RNG regenerates a particle's draws from its counter
-// instead of reading a stored record.
+// Posterior summary of an existing weighted population of records, one pass.
 // ---------------------------------------------------------------------------
-template <bool FROM_RNG>
-__global__ void __launch_bounds__(kTpb) posterior_kernel(
-    PolyParams p, const ppl_poly_particle* __restrict__ rec, const float* __restrict__ lw,
-    int64_t N, uint64_t seed, uint32_t instance, WsHeader* hdr, PostPartial* parts,
-    ppl_is_result* res) {
-  __shared__ float ref[kMaxDegrees][kMaxCoef];
-  __shared__ float dmax[kMaxDegrees];
+constexpr int kPostPpt = 4;
+
+__global__ void __launch_bounds__(kTpb) posterior_kernel(PolyParams p,
+                                                         const ppl_poly_particle* __restrict__ rec,
+                                                         const float* __restrict__ lwin,
+                                                         int64_t N, WsHeader* hdr,
+                                                         DegPartial* parts, ppl_is_result* res) {
+  __shared__ GroupScratch gs;
+  __shared__ DegPartial run[kMaxDegrees];
   const int tid = threadIdx.x;
-  if (tid < kMaxDegrees * kMaxCoef) {
-    const int d = tid / kMaxCoef, k = tid % kMaxCoef;
-    const int j = hdr->deg_arg[d];
-    float v = 0.0f;
-    if (j >= 0) {
-      if (FROM_RNG) {
-        float c[kMaxCoef];
-        poly_draw(p, seed, instance, (uint32_t)j, c);
-        v = c[k];
-      } else {
-        v = rec[j].c[k];
-      }
-    }
-    ref[d][k] = v;
-  }
-  if (tid < kMaxDegrees) dmax[tid] = hdr->deg_max[tid];
+  if (tid < kMaxDegrees) deg_empty(run[tid]);
   __syncthreads();
-
-  float acc[kMaxDegrees][kPostVals];
+  const int64_t group = (int64_t)kTpb * kPostPpt;
+  const int64_t n_groups = (N + group - 1) / group;
+  int nan = 0, bad = 0;
+  for (int64_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
+    float lw[kPostPpt], c[kPostPpt][kMaxCoef];
+    int d[kPostPpt], idx[kPostPpt];
 #pragma unroll
-  for (int d = 0; d < kMaxDegrees; ++d)
+    for (int q = 0; q < kPostPpt; ++q) {
+      const int64_t i = g * group + (int64_t)q * kTpb + tid;
+      idx[q] = (int)i;
+      d[q] = -1;
+      lw[q] = -INFINITY;
 #pragma unroll
-    for (int v = 0; v < kPostVals; ++v) acc[d][v] = 0.0f;
-
-  const int64_t stride = (int64_t)gridDim.x * kTpb;
-  for (int64_t i = (int64_t)blockIdx.x * kTpb + tid; i < N; i += stride) {
-    float c[kMaxCoef];
-    int n;
-    if (FROM_RNG) {
-      n = poly_draw(p, seed, instance, (uint32_t)i, c);
-    } else {
-      const float4* src = reinterpret_cast<const float4*>(rec + i);
-      const float4 a = src[0], b = src[1];
-      c[0] = a.x;
-      c[1] = a.y;
-      c[2] = a.z;
-      c[3] = a.w;
-      c[4] = b.x;
-      c[5] = b.y;
-      n = __float_as_int(b.z);
-    }
-    const int d = n - p.min_deg;
-    if ((unsigned)d >= (unsigned)p.n_deg) {
-      record_status(&hdr->status, PPL_EINVAL);
-      continue;
-    }
-    const float l = lw ? lw[i] : 0.0f;
-    const float w = (l > -INFINITY) ? expf(l - dmax[d]) : 0.0f;
-    float dc[kMaxCoef];
-#pragma unroll
-    for (int k = 0; k < kMaxCoef; ++k) dc[k] = c[k] - ref[d][k];
-#pragma unroll
-    for (int dd = 0; dd < kMaxDegrees; ++dd) {
-      const float wd = (dd == d) ? w : 0.0f;
-      acc[dd][0] += wd;
-#pragma unroll
-      for (int k = 0; k < kMaxCoef; ++k) {
-        const float t = wd * dc[k];
-        acc[dd][1 + k] += t;
-        acc[dd][1 + kMaxCoef + k] = fmaf(t, dc[k], acc[dd][1 + kMaxCoef + k]);
-      }
-    }
-  }
-
-  // block reduction of the 52 sums
-  __shared__ float red[kTpb / 32][kMaxDegrees * kPostVals];
-  const int warp = tid >> 5, lane = tid & 31;
-#pragma unroll
-  for (int d = 0; d < kMaxDegrees; ++d)
-#pragma unroll
-    for (int v = 0; v < kPostVals; ++v) {
-      float x = warp_sum(acc[d][v]);
-      if (lane == 0) red[warp][d * kPostVals + v] = x;
-    }
-  __syncthreads();
-  if (tid < kMaxDegrees * kPostVals) {
-    float x = 0.0f;
-    for (int w = 0; w < kTpb / 32; ++w) x += red[w][tid];
-    parts[blockIdx.x].v[tid / kPostVals][tid % kPostVals] = x;
-  }
-  if (!elect_last_block(&hdr->ticket[1])) return;
-
-  // last block: sum the partials (FP32 over blocks, one warp per value), then
-  // form the summary in FP64
-  __shared__ double tot[kMaxDegrees * kPostVals];
-  for (int v = warp; v < kMaxDegrees * kPostVals; v += kTpb / 32) {
-    float x = 0.0f;
-    for (int b = lane; b < (int)gridDim.x; b += 32) x += parts[b].v[v / kPostVals][v % kPostVals];
-    x = warp_sum(x);
-    if (lane == 0) tot[v] = (double)x;
-  }
-  __syncthreads();
-  if (tid == 0 && res) {
-    const double M = (double)hdr->max_lw;
-    double mass[kMaxDegrees], total = 0.0;
-    bool has[kMaxDegrees];
-    for (int d = 0; d < kMaxDegrees; ++d) {
-      const double S = tot[d * kPostVals];
-      has[d] = d < p.n_deg && hdr->deg_arg[d] >= 0 && S > 0.0;
-      mass[d] = has[d] ? exp((double)dmax[d] - M) * S : 0.0;
-      total += mass[d];
-    }
-    int best = 0;
-    double mean_c[kMaxCoef] = {0, 0, 0, 0, 0, 0};
-    for (int d = 0; d < kMaxDegrees; ++d) {
-      const double S = tot[d * kPostVals];
-      const double pn = total > 0.0 ? mass[d] / total : 0.0;
-      res->p_n[d] = pn;
-      if (d < p.n_deg && pn > res->p_n[best]) best = d;
-      for (int k = 0; k < kMaxCoef; ++k) {
-        double mean = 0.0, var = 0.0;
-        if (has[d]) {  // defined even when the degree's global mass underflows
-          const double A = tot[d * kPostVals + 1 + k] / S;
-          const double B = tot[d * kPostVals + 1 + kMaxCoef + k] / S;
-          mean = (double)ref[d][k] + A;
-          var = fmax(B - A * A, 0.0);
+      for (int k = 0; k < kMaxCoef; ++k) c[q][k] = 0.0f;
+      if (i < N) {
+        const float4* src = reinterpret_cast<const float4*>(rec + i);
+        const float4 a = src[0], b = src[1];
+        c[q][0] = a.x;
+        c[q][1] = a.y;
+        c[q][2] = a.z;
+        c[q][3] = a.w;
+        c[q][4] = b.x;
+        c[q][5] = b.y;
+        const int dd = __float_as_int(b.z) - p.min_deg;
+        if ((unsigned)dd < (unsigned)p.n_deg) {
+          d[q] = dd;
+          lw[q] = lwin ? lwin[i] : 0.0f;
+        } else {
+          bad = 1;
         }
-        res->deg_mean[d][k] = mean;
-        res->deg_var[d][k] = var;
-        mean_c[k] += pn * mean;
       }
     }
-    for (int k = 0; k < kMaxCoef; ++k) res->mean_c[k] = mean_c[k];
-    res->map_deg = p.min_deg + best;
-    res->status = ld_volatile_i32(&hdr->status);
+    group_partial<kPostPpt>(lw, d, idx, c, gs);
+    if (tid < kMaxDegrees) deg_merge(run[tid], gs.out[tid]);
+    if (tid == 0) nan |= gs.nan;
   }
+  __syncthreads();
+  if (tid < kMaxDegrees) parts[blockIdx.x * kMaxDegrees + tid] = run[tid];
+  if (tid == 0 && nan) record_status(&hdr->status, PPL_ENAN);
+  if (bad) record_status(&hdr->status, PPL_EINVAL);
+  if (elect_last_block(&hdr->ticket[1]))
+    finalize_partials(parts, gridDim.x, p.n_deg, p.min_deg, N, hdr, res);
 }
 
 // ---------------------------------------------------------------------------
@@ -307,13 +192,13 @@ int num_sms() {
   return g_num_sms;
 }
 
-constexpr int kTracePpt = 4;
+constexpr int kTraceKernelPpt = 4;
 constexpr int kMaxChunk = 4096;
 
 int trace_grid(int64_t N) {
-  const int64_t groups = (N + (int64_t)kTpb * kTracePpt - 1) / ((int64_t)kTpb * kTracePpt);
-  const int64_t cap = (int64_t)num_sms() * 4;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(groups, std::min<int64_t>(cap, kMaxBlocks)));
+  const int64_t groups =
+      (N + (int64_t)kTpb * kTraceKernelPpt - 1) / ((int64_t)kTpb * kTraceKernelPpt);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(groups, kMaxBlocks));
 }
 
 int stream_grid(int64_t N) {
@@ -326,39 +211,45 @@ cudaError_t launch_poly_trace(const PolyParams& p, const float* x, const float* 
                               int64_t N, uint64_t seed, uint32_t instance, float* lw_out,
                               ppl_poly_particle* rec_out, WsHeader* hdr, void* parts,
                               ppl_is_result* res, cudaStream_t s) {
+  constexpr int PPT = kTraceKernelPpt;
   const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(L, kMaxChunk));
-  const size_t smem = (size_t)chunk * sizeof(float2);
-  const int grid = trace_grid(N);
-  poly_trace_kernel<kTracePpt><<<grid, kTpb, smem, s>>>(p, x, y, L, N, seed, instance, chunk,
-                                                         lw_out, rec_out, hdr,
-                                                         (StatPartial*)parts, res);
+  const size_t smem = trace_smem_bytes<PPT>() + (size_t)chunk * sizeof(float2);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(poly_trace_kernel<PPT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(trace_smem_bytes<PPT>() + kMaxChunk * sizeof(float2)));
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, poly_trace_kernel<PPT>,
+                                                                kTpb, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(trace_grid(N), num_sms() * std::max(1, per_sm)));
+  poly_trace_kernel<PPT><<<grid, kTpb, smem, s>>>(p, x, y, L, N, seed, instance, chunk, lw_out,
+                                                  rec_out, hdr, (DegPartial*)parts, res);
   return cudaGetLastError();
 }
 
-cudaError_t launch_stats(const float* lw, const ppl_poly_particle* rec, int64_t N,
-                         const PolyParams* p, WsHeader* hdr, void* parts, ppl_is_result* res,
+cudaError_t launch_stats(const float* lw, int64_t N, WsHeader* hdr, void* parts,
                          double* lse_out, cudaStream_t s) {
-  PolyParams pp = p ? *p : PolyParams{0, 0, 0, 0.f, 0.f};
-  stats_kernel<<<stream_grid(N), kTpb, 0, s>>>(lw, rec, N, pp, p != nullptr, hdr,
-                                               (StatPartial*)parts, res, lse_out);
+  stats_kernel<<<stream_grid(N), kTpb, 0, s>>>(lw, N, hdr, (StatPartial*)parts, lse_out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_posterior(const PolyParams& p, const ppl_poly_particle* rec, const float* lw,
-                             int64_t N, uint64_t seed, uint32_t instance, WsHeader* hdr,
-                             void* parts, ppl_is_result* res, cudaStream_t s) {
-  const int grid = stream_grid(N);
-  if (rec)
-    posterior_kernel<false><<<grid, kTpb, 0, s>>>(p, rec, lw, N, seed, instance, hdr,
-                                                  (PostPartial*)parts, res);
-  else
-    posterior_kernel<true><<<grid, kTpb, 0, s>>>(p, rec, lw, N, seed, instance, hdr,
-                                                 (PostPartial*)parts, res);
+                             int64_t N, WsHeader* hdr, void* parts, ppl_is_result* res,
+                             cudaStream_t s) {
+  const int64_t groups = (N + (int64_t)kTpb * kPostPpt - 1) / ((int64_t)kTpb * kPostPpt);
+  const int grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>(groups, std::min<int64_t>((int64_t)num_sms() * 4, kMaxBlocks)));
+  posterior_kernel<<<grid, kTpb, 0, s>>>(p, rec, lw, N, hdr, (DegPartial*)parts, res);
   return cudaGetLastError();
 }
 
 size_t partials_bytes() {
-  return (size_t)kMaxBlocks * std::max(sizeof(StatPartial), sizeof(PostPartial));
+  return (size_t)kMaxBlocks * std::max(sizeof(StatPartial), kMaxDegrees * sizeof(DegPartial));
 }
 
 }  // namespace ppl

@@ -22,12 +22,11 @@ cudaError_t launch_poly_trace(const PolyParams& p, const float* x, const float* 
                               int64_t N, uint64_t seed, uint32_t instance, float* lw_out,
                               ppl_poly_particle* rec_out, WsHeader* hdr, void* parts,
                               ppl_is_result* res, cudaStream_t s);
-cudaError_t launch_stats(const float* lw, const ppl_poly_particle* rec, int64_t N,
-                         const PolyParams* p, WsHeader* hdr, void* parts, ppl_is_result* res,
+cudaError_t launch_stats(const float* lw, int64_t N, WsHeader* hdr, void* parts,
                          double* lse_out, cudaStream_t s);
 cudaError_t launch_posterior(const PolyParams& p, const ppl_poly_particle* rec, const float* lw,
-                             int64_t N, uint64_t seed, uint32_t instance, WsHeader* hdr,
-                             void* parts, ppl_is_result* res, cudaStream_t s);
+                             int64_t N, WsHeader* hdr, void* parts, ppl_is_result* res,
+                             cudaStream_t s);
 
 // resample.cu
 constexpr int kScanItems = 8;

@@ -74,7 +74,7 @@ extern "C" ppl_status ppl_resample_noalloc(const float* lw, const uint64_t* q_fi
   // status, tickets, tile counter and this call's tile status words start at zero
   const size_t clear = kNoAllocHeader + (size_t)scan_tiles(n) * sizeof(uint64_t);
   if (cudaMemsetAsync(base, 0, clear, s) != cudaSuccess) return PPL_ECUDA;
-  if (lw && launch_stats(lw, nullptr, n, nullptr, hdr, parts, nullptr, nullptr, s) != cudaSuccess)
+  if (lw && launch_stats(lw, n, hdr, parts, nullptr, s) != cudaSuccess)
     return PPL_ECUDA;
   if (launch_resample_scan(lw, q_fixed, n, m, seed, instance, t, hdr, tiles, prefix, nullptr,
                            s) != cudaSuccess)

@@ -1,0 +1,287 @@
+// One-pass posterior reduction of weighted line-fitting traces (§3.6.2 the
+// normalisation of the log-weights; Fig. 1 the returned coefficients).
+//
+// A group of traces (one block's particles of one instance) is reduced to a
+// per-degree partial: the best log-weight m and its index, S = sum exp(lw - m),
+// S2 = sum exp(2 (lw - m)), and the weighted mean and second central moment
+// M2 = sum w (c - mean)^2 of every coefficient.  Within a group the moments are
+// formed around the group's best trace of that degree (a shift that keeps the
+// FP32 sums well conditioned), and partials merge exactly in real arithmetic:
+// rescale by exp(m_a - m), then combine means and M2 by the parallel-variance
+// rule (Chan, Golub and LeVeque 1979).  The LSE, ESS, degree masses and pooled
+// moments all follow from the per-degree partials.
+#pragma once
+
+#include "common.cuh"
+#include "poly.cuh"
+
+namespace ppl {
+
+struct __align__(16) DegPartial {
+  float m;
+  int arg;
+  float S, S2;
+  float mean[kMaxCoef];
+  float M2[kMaxCoef];
+};
+
+__device__ __forceinline__ void deg_empty(DegPartial& p) {
+  p.m = -INFINITY;
+  p.arg = 0x7fffffff;
+  p.S = 0.0f;
+  p.S2 = 0.0f;
+#pragma unroll
+  for (int k = 0; k < kMaxCoef; ++k) {
+    p.mean[k] = 0.0f;
+    p.M2[k] = 0.0f;
+  }
+}
+
+// a <- merge(a, b)
+__device__ __forceinline__ void deg_merge(DegPartial& a, const DegPartial& b) {
+  if (b.m == -INFINITY) return;
+  if (a.m == -INFINITY) {
+    a = b;
+    return;
+  }
+  const float M = fmaxf(a.m, b.m);
+  const float ea = expf(a.m - M), eb = expf(b.m - M);
+  const float wa = a.S * ea, wb = b.S * eb, w = wa + wb;
+  const float fb = wb / w, cross = wa * fb;
+#pragma unroll
+  for (int k = 0; k < kMaxCoef; ++k) {
+    const float d = b.mean[k] - a.mean[k];
+    a.mean[k] = fmaf(d, fb, a.mean[k]);
+    a.M2[k] = fmaf(d * d, cross, fmaf(a.M2[k], ea, b.M2[k] * eb));
+  }
+  a.S2 = fmaf(a.S2, ea * ea, b.S2 * eb * eb);
+  a.S = w;
+  if (b.m > a.m || (b.m == a.m && b.arg < a.arg)) a.arg = b.arg;
+  a.m = M;
+}
+
+__device__ __forceinline__ DegPartial deg_shfl_xor(const DegPartial& p, int mask) {
+  DegPartial o;
+  o.m = __shfl_xor_sync(0xffffffffu, p.m, mask);
+  o.arg = __shfl_xor_sync(0xffffffffu, p.arg, mask);
+  o.S = __shfl_xor_sync(0xffffffffu, p.S, mask);
+  o.S2 = __shfl_xor_sync(0xffffffffu, p.S2, mask);
+#pragma unroll
+  for (int k = 0; k < kMaxCoef; ++k) {
+    o.mean[k] = __shfl_xor_sync(0xffffffffu, p.mean[k], mask);
+    o.M2[k] = __shfl_xor_sync(0xffffffffu, p.M2[k], mask);
+  }
+  return o;
+}
+
+// Load a partial written by another block of the running kernel, from L2.
+__device__ __forceinline__ DegPartial ld_partial_cg(const DegPartial* src) {
+  static_assert(sizeof(DegPartial) == 64, "DegPartial is four 16-byte words");
+  DegPartial o;
+  const float4* s = reinterpret_cast<const float4*>(src);
+  float4* d = reinterpret_cast<float4*>(&o);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) d[i] = __ldcg(s + i);
+  return o;
+}
+
+// Shared-memory scratch of group_partial.
+struct GroupScratch {
+  float wmax[kTpb / 32][kMaxDegrees];
+  int warg[kTpb / 32][kMaxDegrees];
+  float bmax[kMaxDegrees];
+  int barg[kMaxDegrees];
+  float ref[kMaxDegrees][kMaxCoef];
+  float sums[kTpb / 32][kMaxDegrees * (2 + 2 * kMaxCoef)];
+  DegPartial out[kMaxDegrees];
+  int nan;
+};
+
+// Reduce PPT traces per thread (lw, degree index d in [0, 4) or -1 when the
+// slot is empty, coefficients c) over the block into gs.out[0..3].  Every
+// thread of the block must call it.  Indices passed as `idx` are global trace
+// indices (lowest wins ties).
+template <int PPT>
+__device__ __forceinline__ void group_partial(const float (&lw)[PPT], const int (&d)[PPT],
+                                              const int (&idx)[PPT],
+                                              const float (&c)[PPT][kMaxCoef],
+                                              GroupScratch& gs) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // 1. best trace of every degree
+  float m[kMaxDegrees];
+  int a[kMaxDegrees];
+  int nan = 0;
+#pragma unroll
+  for (int k = 0; k < kMaxDegrees; ++k) {
+    m[k] = -INFINITY;
+    a[k] = 0x7fffffff;
+  }
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    nan |= (d[q] >= 0) & (lw[q] != lw[q]);
+#pragma unroll
+    for (int k = 0; k < kMaxDegrees; ++k)
+      if (d[q] == k && (lw[q] > m[k] || (lw[q] == m[k] && idx[q] < a[k]))) {
+        m[k] = lw[q];
+        a[k] = idx[q];
+      }
+  }
+#pragma unroll
+  for (int k = 0; k < kMaxDegrees; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float om = __shfl_xor_sync(0xffffffffu, m[k], o);
+      const int oa = __shfl_xor_sync(0xffffffffu, a[k], o);
+      if (om > m[k] || (om == m[k] && oa < a[k])) {
+        m[k] = om;
+        a[k] = oa;
+      }
+    }
+    if (lane == 0) {
+      gs.wmax[warp][k] = m[k];
+      gs.warg[warp][k] = a[k];
+    }
+  }
+  nan = __any_sync(0xffffffffu, nan);
+  if (tid == 0) gs.nan = 0;
+  __syncthreads();
+  if (lane == 0 && nan) gs.nan = 1;
+  if (tid < kMaxDegrees) {
+    float bm = -INFINITY;
+    int ba = 0x7fffffff;
+    for (int w = 0; w < kTpb / 32; ++w)
+      if (gs.wmax[w][tid] > bm || (gs.wmax[w][tid] == bm && gs.warg[w][tid] < ba)) {
+        bm = gs.wmax[w][tid];
+        ba = gs.warg[w][tid];
+      }
+    gs.bmax[tid] = bm;
+    gs.barg[tid] = ba;
+  }
+  __syncthreads();
+  // 2. the best trace's coefficients become the shift of its degree
+#pragma unroll
+  for (int q = 0; q < PPT; ++q)
+    if (d[q] >= 0 && idx[q] == gs.barg[d[q]])
+#pragma unroll
+      for (int k = 0; k < kMaxCoef; ++k) gs.ref[d[q]][k] = c[q][k];
+  __syncthreads();
+  // 3. weighted sums around the shift
+  constexpr int V = 2 + 2 * kMaxCoef;
+  float acc[kMaxDegrees][V];
+#pragma unroll
+  for (int k = 0; k < kMaxDegrees; ++k)
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[k][v] = 0.0f;
+#pragma unroll
+  for (int q = 0; q < PPT; ++q) {
+    if (d[q] < 0) continue;
+    const int dd = d[q];
+    const float w = (lw[q] > -INFINITY) ? expf(lw[q] - gs.bmax[dd]) : 0.0f;
+    float dc[kMaxCoef];
+#pragma unroll
+    for (int k = 0; k < kMaxCoef; ++k) dc[k] = c[q][k] - gs.ref[dd][k];
+#pragma unroll
+    for (int k = 0; k < kMaxDegrees; ++k) {
+      const float wk = (k == dd) ? w : 0.0f;
+      acc[k][0] += wk;
+      acc[k][1] = fmaf(wk, wk, acc[k][1]);
+#pragma unroll
+      for (int j = 0; j < kMaxCoef; ++j) {
+        const float t = wk * dc[j];
+        acc[k][2 + j] += t;
+        acc[k][2 + kMaxCoef + j] = fmaf(t, dc[j], acc[k][2 + kMaxCoef + j]);
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kMaxDegrees; ++k)
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const float x = warp_sum(acc[k][v]);
+      if (lane == 0) gs.sums[warp][k * V + v] = x;
+    }
+  __syncthreads();
+  // 4. one thread per degree forms the partial
+  if (tid < kMaxDegrees) {
+    const int k = tid;
+    float tot[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      float x = 0.0f;
+      for (int w = 0; w < kTpb / 32; ++w) x += gs.sums[w][k * V + v];
+      tot[v] = x;
+    }
+    DegPartial& p = gs.out[k];
+    p.m = gs.bmax[k];
+    p.arg = gs.barg[k];
+    p.S = tot[0];
+    p.S2 = tot[1];
+    if (p.m == -INFINITY || !(tot[0] > 0.0f)) {
+      deg_empty(p);
+      p.m = gs.bmax[k];
+      p.arg = gs.barg[k];
+    } else {
+#pragma unroll
+      for (int j = 0; j < kMaxCoef; ++j) {
+        const float A = tot[2 + j] / tot[0];
+        p.mean[j] = gs.ref[k][j] + A;
+        p.M2[j] = fmaxf(tot[2 + kMaxCoef + j] - A * tot[2 + j], 0.0f);
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Summary of a population from its four per-degree partials, in FP64.
+// S and S2 are the per-degree sums already combined in FP64 by the caller.
+__device__ __forceinline__ void write_summary(const DegPartial (&p)[kMaxDegrees],
+                                              const double (&S)[kMaxDegrees],
+                                              const double (&S2)[kMaxDegrees], int n_deg,
+                                              int min_deg, int64_t N, int32_t status,
+                                              ppl_is_result* res) {
+  double M = -INFINITY;
+  int64_t arg = -1;
+  for (int k = 0; k < n_deg; ++k)
+    if (p[k].m != -INFINITY &&
+        ((double)p[k].m > M || ((double)p[k].m == M && p[k].arg < arg))) {
+      M = p[k].m;
+      arg = p[k].arg;
+    }
+  double s = 0.0, s2 = 0.0, mass[kMaxDegrees];
+  for (int k = 0; k < kMaxDegrees; ++k) {
+    mass[k] = 0.0;
+    if (k < n_deg && p[k].m != -INFINITY && S[k] > 0.0) {
+      const double e = exp((double)p[k].m - M);
+      mass[k] = e * S[k];
+      s += mass[k];
+      s2 += e * e * S2[k];
+    }
+  }
+  res->lse = M + log(s);
+  res->log_z = res->lse - log((double)N);
+  res->ess = s * s / s2;
+  res->max_lw = M;
+  res->argmax = arg;
+  res->n_particles = N;
+  res->n_deg = n_deg;
+  int best = 0;
+  for (int j = 0; j < kMaxCoef; ++j) res->mean_c[j] = 0.0;
+  for (int k = 0; k < kMaxDegrees; ++k) {
+    const bool has = k < n_deg && p[k].m != -INFINITY;
+    const double pn = s > 0.0 ? mass[k] / s : 0.0;
+    res->p_n[k] = pn;
+    if (k < n_deg && pn > res->p_n[best]) best = k;
+    res->deg_max_lw[k] = has ? (double)p[k].m : -INFINITY;
+    res->deg_argmax[k] = has ? p[k].arg : -1;
+    for (int j = 0; j < kMaxCoef; ++j) {
+      const bool ok = has && S[k] > 0.0 && p[k].S > 0.0f;
+      res->deg_mean[k][j] = ok ? (double)p[k].mean[j] : 0.0;
+      res->deg_var[k][j] = ok ? (double)p[k].M2[j] / (double)p[k].S : 0.0;
+      res->mean_c[j] += pn * res->deg_mean[k][j];
+    }
+  }
+  res->map_deg = min_deg + best;
+  res->status = status;
+}
+
+}  // namespace ppl

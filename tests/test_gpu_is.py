@@ -2,8 +2,8 @@
 posterior summary) with the FP64 oracle at equal seeds.
 
 Tolerances: discrete draws bit-exact; coefficients and log-weights within the
-FP32 error of the traces; |delta log Z| <= 1e-3 (plus two FP32 ulps of the
-largest log-weight, which only matters when |max lw| > 2000); degree masses
+FP32 error of the traces; |delta log Z| <= 1e-3 (plus four FP32 ulps of the
+largest log-weight, which only matters when |max lw| > 1000); degree masses
 and weighted coefficient means within 1e-4 relative.
 """
 import numpy as np
@@ -29,9 +29,9 @@ def _check(orc, res, lw, n, c, origin, x, y, N, seed, model_kw, full=True):
     assert np.allclose(c, c_r, rtol=1e-5, atol=1e-4)              # FP32 Box-Muller
     err = np.abs(lw.astype(np.float64) - lw_r)
     assert np.all(err <= 4e-6 * np.abs(lw_r) + 1e-3), float(np.max(err - 4e-6 * np.abs(lw_r)))
-    # 1e-3, widened by two FP32 ulps of the largest log-weight for data sets
+    # 1e-3, widened by four FP32 ulps of the largest log-weight for data sets
     # whose log-weights are so large that FP32 cannot resolve 1e-3
-    assert abs(res["log_z"] - ref["log_z"]) <= 1e-3 + 2.0 ** -22 * abs(ref["max_lw"])
+    assert abs(res["log_z"] - ref["log_z"]) <= 1e-3 + 2.0 ** -21 * abs(ref["max_lw"])
     assert res["ess"] == pytest.approx(ref["ess"], rel=1e-3)
     assert res["max_lw"] == pytest.approx(ref["max_lw"], rel=4e-6, abs=1e-3)
     if res["argmax"] != ref["argmax"]:  # a near-tie may order differently in FP32
