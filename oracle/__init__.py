@@ -107,7 +107,7 @@ def lib():
             f.restype = res
             f.argtypes = args
         _LIB = L
-        from . import mlp as _mlp  # noqa: F401  (registers the MLP signatures)
+        from . import mlp as _mlp
         _mlp._register(L)
     return _LIB
 

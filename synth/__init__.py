@@ -120,3 +120,18 @@ def fixed_weights(N, seed, max_bits=40):
     q = rng.integers(0, 2 ** bits, N, dtype=np.uint64)
     q[rng.random(N) < 0.3] = 0
     return q
+
+
+def mlp_weights(seed, sizes=((256, 64), (256, 256), (48, 256)), bias_scale=0.05):
+    """Seeded network parameters: W uniform in +-1/sqrt(fan_in) rounded to values
+    BF16 represents exactly (ties to even), biases uniform in +-bias_scale, FP32."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for n_out, n_in in sizes:
+        w = rng.uniform(-1.0, 1.0, (n_out, n_in)) / np.sqrt(n_in)
+        w = w.astype(np.float32)
+        bits = w.view(np.uint32).astype(np.uint64)
+        bits = (bits + 0x7FFF + ((bits >> 16) & 1)) & 0xFFFF0000
+        out.append(bits.astype(np.uint32).view(np.float32).reshape(n_out, n_in))
+        out.append(rng.uniform(-bias_scale, bias_scale, n_out).astype(np.float32))
+    return out
