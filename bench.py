@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the state-space, batched and learned-proposal workloads")
     ap.add_argument("--particles", type=int, default=N_PARTICLES,
                     help="particles per step (smaller cases for profiling only)")
     return ap.parse_args()
@@ -160,6 +162,169 @@ def cpu_baseline(n_sample=1 << 22):
             "sample": f"{n_sample} particles x {N_POINTS} points, full step (traces, posterior, "
                       f"resample, gather), FP64 C with OpenMP over {threads} threads, "
                       f"{dt:.2f} s"}
+
+
+# --------------------------------------------------------------------------
+# The other workloads of the path, measured in the same run (rank 0).
+# --------------------------------------------------------------------------
+def _event_ms(torch, fn, reps):
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def bench_smc(torch, ppl, reps=5):
+    """Bootstrap filter on the linear-Gaussian model, T = 200, 2^20 particles, one CUDA graph."""
+    import numpy as np
+
+    import synth
+    N, T = 1 << 20, 200
+    y = synth.lgssm_dataset(T, 2)
+    model = ppl.lgssm_model()
+    x = torch.zeros(N, dtype=torch.float32, device="cuda")
+    lw = torch.zeros_like(x)
+    acc = torch.zeros(1, dtype=torch.float64, device="cuda")
+    flags = torch.zeros(T, dtype=torch.int32, device="cuda")
+    est = torch.zeros((T, 2), dtype=torch.float64, device="cuda")
+    ws = ppl.workspace(model, N)
+
+    def run_steps():
+        for t in range(1, T + 1):
+            ppl.ppl_smc_step(model, float(y[t - 1]), t, 2, x, lw, acc, flags[t - 1:t], est[t - 1],
+                             ws)
+
+    def reset():
+        x.zero_()
+        lw.zero_()
+        acc.zero_()
+
+    reset()
+    run_steps()  # warm-up outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    cs = torch.cuda.Stream()
+    with torch.cuda.graph(g, stream=cs):
+        run_steps()
+    times = []
+    for _ in range(reps):
+        reset()
+        torch.cuda.synchronize()
+        times.append(_event_ms(torch, g.replay, 1))
+    ms = float(np.median(times))
+    logz = float(est[-1, 0])
+    import oracle
+    kal = oracle.kalman_logz(oracle.lgssm_model(), y)
+    return {"workload": "bootstrap filter, linear-Gaussian SSM, T=200, 2^20 particles, FP32 "
+                        "state, resample when ESS < N/2; 200 steps in one CUDA graph",
+            "metric": "particle-steps/sec", "value": N * T / (ms / 1e3), "unit": "particle-steps/s",
+            "ms_per_filter": ms, "resampling_steps": int(flags.sum().item()), "log_z": logz,
+            "kalman_log_z": kal, "abs_err_vs_kalman": abs(logz - kal),
+            "gpu_launches_per_filter": 5 * T}
+
+
+def bench_batched(torch, ppl, reps=5):
+    """4096 uneven line-fitting instances in one persistent launch, autotuned, graph-replayed."""
+    import numpy as np
+
+    import synth
+    inst = synth.batched_instances(4096, 3)
+    model = ppl.poly_model()
+    x, y = torch.from_numpy(inst["x"]).cuda(), torch.from_numpy(inst["y"]).cuda()
+    doff = torch.from_numpy(inst["data_off"]).cuda()
+    poff = torch.from_numpy(inst["part_off"]).cuda()
+    ws = ppl.batched_workspace(inst["data_off"], inst["part_off"])
+    out = ppl.batch_results_tensor(4096)
+    cache = os.path.join(ROOT, "paper_2010_08454_gb300", "_build", "batched_tune.json")
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
+    plan = ppl.ppl_batched_autotune(model, x, y, doff, poff, inst["data_off"], inst["part_off"],
+                                    3, out, ws, cache)
+    g = torch.cuda.CUDAGraph()
+    cs = torch.cuda.Stream()
+    ppl.ppl_infer_is_batched(model, x, y, doff, poff, 3, plan, out, ws)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=cs):
+        ppl.ppl_infer_is_batched(model, x, y, doff, poff, 3, plan, out, ws)
+    g.replay()
+    torch.cuda.synchronize()
+    ms = _event_ms(torch, g.replay, reps)
+    res = ppl.read_batch_results(out, 4096)
+    status = max(r["status"] for r in res)
+    n_traces = int(inst["part_off"][-1])
+    # expected FP32 flops of the factor under the degree prior: (2 ncoef + 1), mean ncoef 4.5
+    flops = float(plan.work) * 10.0
+    return {"workload": "4096 line-fitting instances, data lengths log-uniform [16, 4096], "
+                        "particles log-uniform [2^10, 2^16], one persistent launch in a CUDA graph",
+            "metric": "particle-traces/sec", "value": n_traces / (ms / 1e3), "unit": "traces/s",
+            "ms_per_launch": ms, "traces": n_traces, "trace_points": float(plan.work),
+            "fp32_tflops": flops / (ms / 1e3) / 1e12,
+            "autotuned": {"ppt": plan.ppt, "blocks_per_sm": plan.blocks_per_sm},
+            "items": int(plan.n_items), "status": status}
+
+
+def bench_learned(torch, ppl, epochs=4, n_sets=1024, N=1 << 20, reps=3):
+    """Learned vs prior proposal: ESS/sec at |delta log Z| < 0.05 on held-out data sets."""
+    import numpy as np
+
+    import oracle
+    import synth
+    model = ppl.poly_model()
+    params = ppl.pack_params(synth.mlp_weights(1))
+    am, av = torch.zeros_like(params), torch.zeros_like(params)
+    n_pairs, batch = 1 << 20, 1024
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ppl.ppl_proposal_train(model, params, am, av, n_pairs, batch, epochs, 99, 1e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    d = synth.prior_datasets(n_sets, 32, 4)
+    x, y = torch.from_numpy(d["x"]).cuda(), torch.from_numpy(d["y"]).cuda()
+    xf, yf = x.reshape(-1).contiguous(), y.reshape(-1).contiguous()
+    doff_h = np.arange(n_sets + 1, dtype=np.int64) * 32
+    poff_h = np.arange(n_sets + 1, dtype=np.int64) * N
+    doff, poff = torch.from_numpy(doff_h).cuda(), torch.from_numpy(poff_h).cuda()
+    ws = ppl.batched_workspace(doff_h, poff_h)
+    plan = ppl.ppl_batched_prepare(model, doff_h, poff_h, 8, 2, ws)
+    pws = ppl.proposal_workspace(n_sets)
+    prop = torch.empty((n_sets, 48), dtype=torch.float32, device="cuda")
+    out_l, out_p = ppl.batch_results_tensor(n_sets), ppl.batch_results_tensor(n_sets)
+
+    def learned():
+        ppl.ppl_proposal_forward(model, params, x, y, out=prop, ws=pws)
+        ppl.ppl_infer_is_learned(model, xf, yf, doff, poff, 5, plan, prop, out_l, ws)
+
+    def prior():
+        ppl.ppl_infer_is_batched(model, xf, yf, doff, poff, 5, plan, out_p, ws)
+
+    learned()
+    prior()
+    ms_l = _event_ms(torch, learned, reps)
+    ms_p = _event_ms(torch, prior, reps)
+    rl, rp = ppl.read_batch_results(out_l, n_sets), ppl.read_batch_results(out_p, n_sets)
+    om = oracle.poly_model()
+    exact = np.array([oracle.poly_exact(om, d["x"][b], d["y"][b])["log_z"] for b in range(n_sets)])
+    el = np.abs(np.array([r["log_z"] for r in rl]) - exact)
+    ep = np.abs(np.array([r["log_z"] for r in rp]) - exact)
+    ess_l = np.array([r["ess"] for r in rl])
+    ess_p = np.array([r["ess"] for r in rp])
+    ok_l, ok_p = el < 0.05, ep < 0.05
+    return {"workload": f"{n_sets} held-out data sets from the model (32 points), {N} particles "
+                        f"each; proposal network trained on {n_pairs} forward-simulated pairs x "
+                        f"{epochs} epochs",
+            "metric": "ESS/sec at |delta log Z| < 0.05", "unit": "ESS/s",
+            "learned": {"ess_per_sec": float(ess_l.sum() / (ms_l / 1e3)),
+                        "ess_per_sec_at_tol": float(ess_l[ok_l].sum() / (ms_l / 1e3)),
+                        "frac_within_0.05": float(ok_l.mean()), "median_abs_err": float(np.median(el)),
+                        "median_ess": float(np.median(ess_l)), "ms": ms_l},
+            "prior": {"ess_per_sec": float(ess_p.sum() / (ms_p / 1e3)),
+                      "ess_per_sec_at_tol": float(ess_p[ok_p].sum() / (ms_p / 1e3)),
+                      "frac_within_0.05": float(ok_p.mean()), "median_abs_err": float(np.median(ep)),
+                      "median_ess": float(np.median(ess_p)), "ms": ms_p},
+            "train_seconds": train_s, "train_steps": epochs * (n_pairs // batch)}
 
 
 def run_reference(args):
@@ -347,6 +512,10 @@ def run_ours(args):
         "result": {"log_z": summary["log_z"], "ess": summary["ess"], "map_deg": summary["map_deg"]},
         "wall_s": t_wall,
     }
+    if not args.no_configs:
+        out["configs"] = {"smc_lgssm_T200_2e20": bench_smc(torch, ppl),
+                          "batched_4096": bench_batched(torch, ppl),
+                          "learned_proposal_1024x2e20": bench_learned(torch, ppl)}
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline()
     print(json.dumps(out), flush=True)

@@ -233,6 +233,50 @@ ppl_status ppl_batched_autotune(const ppl_model* model, const float* x, const fl
                                 ppl_stream stream);
 ppl_status ppl_batched_status(const void* ws, ppl_stream stream);
 
+/* Learned proposal (inference compilation: Le, Baydin and Wood, AISTATS 2017).
+ * A network maps a 32-point line-fitting data set to a proposal q(n, c | data)
+ * over the trace's random choices; importance weights p/q correct it to the
+ * posterior (§3.6.2).  Network: in[64] = the points sorted by x, (x, y/10),
+ * BF16; h1 = relu(W1 in + b1), h2 = relu(W2 h1 + b2) with 256 units, out =
+ * W3 h2 + b3 with 48 outputs; BF16 weights and activations on the tensor
+ * cores, FP32 accumulation, FP32 biases.  out[0..n_deg) are degree logits;
+ * coefficient j of degree slot k (slots in order, ncoef_k = min_deg + k +
+ * coef_offset) has mu = prior_sigma out[4 + 2 i], s = prior_sigma exp(clamp(
+ * out[5 + 2 i], -9, 1)), i = ncoef_0 + .. + ncoef_{k-1} + j.
+ * params [dev, FP32, ppl_proposal_num_params()] = W1 | b1 | W2 | b2 | W3 | b3
+ * (row-major [out x in]).  Training pairs are forward simulations of the model
+ * (purpose FORWARD_SIM): pair p draws a prior trace and 32 points x ~ U[-1, 1],
+ * y = f(x) + obs_sigma e.
+ *  ppl_proposal_features: BF16 features [dev, n_sets x 64] of x, y [n_sets x 32].
+ *  ppl_proposal_forward: out_dev [dev, FP32, n_sets x 48] for data sets x, y.
+ *  ppl_proposal_grad: gradient [dev, FP32] of the mean -log q over pairs
+ *    pair0 .. pair0 + batch - 1, and the summed loss in loss_out [dev, FP64].
+ *  ppl_proposal_train: Adam (lr, 0.9, 0.999, 1e-8) on params with moments
+ *    adam_m, adam_v [dev, FP32, zero-initialised], epochs x (n_pairs / batch)
+ *    steps over pairs 0 .. n_pairs - 1; loss_per_step [dev, FP64] optional.
+ *  ppl_infer_is_learned: ppl_infer_is_batched with each instance's draws from
+ *    its proposal (proposal [dev, FP32, n_inst x 48], e.g. from
+ *    ppl_proposal_forward); a proposal equal to the prior gives the prior run. */
+int64_t ppl_proposal_num_params(void);
+size_t ppl_proposal_workspace_size(int32_t batch);
+ppl_status ppl_proposal_features(const float* x, const float* y, int32_t n_sets, void* feat_dev,
+                                 ppl_stream stream);
+ppl_status ppl_proposal_forward(const ppl_model* model, const float* params, const float* x,
+                                const float* y, int32_t n_sets, float* out_dev, void* ws,
+                                size_t ws_bytes, ppl_stream stream);
+ppl_status ppl_proposal_grad(const ppl_model* model, const float* params, int64_t pair0,
+                             int32_t batch, uint64_t seed, float* grad_out, double* loss_out,
+                             void* ws, size_t ws_bytes, ppl_stream stream);
+ppl_status ppl_proposal_train(const ppl_model* model, float* params, float* adam_m,
+                              float* adam_v, int64_t n_pairs, int32_t batch, int32_t epochs,
+                              uint64_t seed, float lr, double* loss_per_step, void* ws,
+                              size_t ws_bytes, ppl_stream stream);
+ppl_status ppl_infer_is_learned(const ppl_model* model, const float* x, const float* y,
+                                const int64_t* data_off, const int64_t* part_off,
+                                int32_t n_inst, uint64_t seed, const ppl_batch_plan* plan,
+                                const float* proposal, ppl_is_result* out_dev, void* ws,
+                                size_t ws_bytes, ppl_stream stream);
+
 /* ppl_resample without a workspace, for callers that cannot allocate device
  * memory: a plugin whose host application owns every device allocation
  * through its own pool, or a real-time loop that must not risk the implicit

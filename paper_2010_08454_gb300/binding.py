@@ -122,6 +122,27 @@ _SIGS = {
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                             ctypes.c_char_p, ctypes.c_void_p, ctypes.c_void_p]),
     "ppl_batched_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "ppl_proposal_num_params": (ctypes.c_int64, []),
+    "ppl_proposal_workspace_size": (ctypes.c_size_t, [ctypes.c_int32]),
+    "ppl_proposal_features": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                             ctypes.c_void_p, ctypes.c_void_p]),
+    "ppl_proposal_forward": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "ppl_proposal_grad": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                         ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                         ctypes.c_void_p]),
+    "ppl_proposal_train": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_uint64, ctypes.c_float,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                          ctypes.c_void_p]),
+    "ppl_infer_is_learned": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                            ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                            ctypes.c_void_p]),
     "ppl_posterior_reduce": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_size_t, ctypes.c_void_p]),
@@ -412,3 +433,69 @@ def batch_results_tensor(n_inst, device="cuda"):
 def read_batch_results(out, n_inst):
     raw = out.detach().cpu().numpy().tobytes()
     return [PplIsResult.from_buffer_copy(raw, i * RESULT_BYTES).as_dict() for i in range(n_inst)]
+
+
+# ---- learned proposal ---------------------------------------------------
+def ppl_proposal_num_params():
+    return int(lib().ppl_proposal_num_params())
+
+
+def proposal_workspace(batch, device="cuda"):
+    return torch.empty(int(lib().ppl_proposal_workspace_size(int(batch))), dtype=torch.uint8,
+                       device=device)
+
+
+def pack_params(weights, device="cuda"):
+    """[W1, b1, W2, b2, W3, b3] (numpy or torch) -> one FP32 device buffer."""
+    flat = [torch.as_tensor(np.asarray(w, dtype=np.float32)).reshape(-1) for w in weights]
+    return torch.cat(flat).to(device)
+
+
+def ppl_proposal_features(x, y, stream=None):
+    n_sets = x.shape[0]
+    feat = torch.empty((n_sets, 64), dtype=torch.bfloat16, device=x.device)
+    _check(lib().ppl_proposal_features(_ptr(x), _ptr(y), n_sets, _ptr(feat), _stream(stream)),
+           "ppl_proposal_features")
+    return feat
+
+
+def ppl_proposal_forward(model, params, x, y, out=None, ws=None, stream=None):
+    n_sets = x.shape[0]
+    if ws is None:
+        ws = proposal_workspace(n_sets, x.device)
+    if out is None:
+        out = torch.empty((n_sets, 48), dtype=torch.float32, device=x.device)
+    _check(lib().ppl_proposal_forward(ctypes.byref(model), _ptr(params), _ptr(x), _ptr(y),
+                                      n_sets, _ptr(out), _ptr(ws), ws.numel(), _stream(stream)),
+           "ppl_proposal_forward")
+    return out
+
+
+def ppl_proposal_grad(model, params, pair0, batch, seed, ws=None, stream=None):
+    if ws is None:
+        ws = proposal_workspace(batch, params.device)
+    grad = torch.empty_like(params)
+    loss = torch.zeros(1, dtype=torch.float64, device=params.device)
+    _check(lib().ppl_proposal_grad(ctypes.byref(model), _ptr(params), int(pair0), int(batch),
+                                   ctypes.c_uint64(seed), _ptr(grad), _ptr(loss), _ptr(ws),
+                                   ws.numel(), _stream(stream)), "ppl_proposal_grad")
+    return grad, loss
+
+
+def ppl_proposal_train(model, params, adam_m, adam_v, n_pairs, batch, epochs, seed, lr=1e-3,
+                       loss_per_step=None, ws=None, stream=None):
+    if ws is None:
+        ws = proposal_workspace(batch, params.device)
+    _check(lib().ppl_proposal_train(ctypes.byref(model), _ptr(params), _ptr(adam_m),
+                                    _ptr(adam_v), int(n_pairs), int(batch), int(epochs),
+                                    ctypes.c_uint64(seed), float(lr), _ptr(loss_per_step),
+                                    _ptr(ws), ws.numel(), _stream(stream)), "ppl_proposal_train")
+
+
+def ppl_infer_is_learned(model, x, y, data_off, part_off, seed, plan, proposal, out, ws,
+                         stream=None):
+    _check(lib().ppl_infer_is_learned(ctypes.byref(model), _ptr(x), _ptr(y), _ptr(data_off),
+                                      _ptr(part_off), plan.n_inst, ctypes.c_uint64(seed),
+                                      ctypes.byref(plan), _ptr(proposal), _ptr(out), _ptr(ws),
+                                      ws.numel(), _stream(stream)), "ppl_infer_is_learned")
+    return out

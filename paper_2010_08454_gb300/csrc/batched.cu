@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "learned.cuh"
 #include "posterior.cuh"
 #include "trace.cuh"
 
@@ -58,12 +59,13 @@ static BatchLayout batch_layout(int64_t n_items, int32_t n_inst) {
 
 constexpr int kBatchChunk = 4096;  // data points staged in shared memory at a time
 
-template <int PPT>
+template <int PPT, bool LEARNED>
 __global__ void __launch_bounds__(kTpb) batched_kernel(
     PolyParams p, const float* __restrict__ xs, const float* __restrict__ ys,
     const int64_t* __restrict__ data_off, const int64_t* __restrict__ part_off,
     const BatchItem* __restrict__ items, int64_t n_items, const int32_t* __restrict__ first,
-    int32_t* count, uint64_t seed, WsHeader* hdr, DegPartial* parts, ppl_is_result* out) {
+    int32_t* count, uint64_t seed, const float* __restrict__ proposal, WsHeader* hdr,
+    DegPartial* parts, ppl_is_result* out) {
   extern __shared__ __align__(16) unsigned char smem[];
   TraceSmem<PPT>& ts = *reinterpret_cast<TraceSmem<PPT>*>(smem);
   float2* sdata = reinterpret_cast<float2*>(smem + trace_smem_bytes<PPT>());
@@ -71,8 +73,10 @@ __global__ void __launch_bounds__(kTpb) batched_kernel(
   __shared__ double fS[kMaxDegrees], fS2[kMaxDegrees];
   __shared__ int64_t item_sh;
   __shared__ bool last_sh;
+  __shared__ ProposalSmem prop;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int cur = -1;  // instance whose data is staged
+  int cur = -1;      // instance whose data is staged
+  int cur_prop = -1;  // instance whose proposal is loaded
   while (true) {
     if (tid == 0) item_sh = (int64_t)atomicAdd(&hdr->tile_counter[1], 1u);
     __syncthreads();
@@ -89,9 +93,20 @@ __global__ void __launch_bounds__(kTpb) batched_kernel(
     } else if (!resident) {
       cur = -1;  // the chunks overwrite the staged data
     }
-    trace_group<PPT>(p, xs + d0, ys + d0, L, kBatchChunk, resident, sdata, N,
-                     (int64_t)items[it].tile * kTpb * PPT, seed, (uint32_t)b, nullptr, nullptr,
-                     ts, gout);
+    const int64_t tbase = (int64_t)items[it].tile * kTpb * PPT;
+    if (LEARNED) {
+      if (b != cur_prop) {
+        __syncthreads();
+        if (tid == 0) load_proposal(p, proposal + (int64_t)b * 48, prop);
+        __syncthreads();
+        cur_prop = b;
+      }
+      trace_group<PPT>(LearnedDraw{p, seed, (uint32_t)b, &prop}, p, xs + d0, ys + d0, L,
+                       kBatchChunk, resident, sdata, N, tbase, nullptr, nullptr, ts, gout);
+    } else {
+      trace_group<PPT>(PriorDraw{p, seed, (uint32_t)b}, p, xs + d0, ys + d0, L, kBatchChunk,
+                       resident, sdata, N, tbase, nullptr, nullptr, ts, gout);
+    }
     if (tid < kMaxDegrees) parts[it * kMaxDegrees + tid] = gout[tid];
     if (tid == 0 && ts.nan) record_status(&hdr->status, PPL_ENAN);
     // the last item of the instance merges the instance's partials
@@ -147,12 +162,12 @@ __global__ void __launch_bounds__(kTpb) batched_kernel(
   }
 }
 
-template <int PPT>
+template <int PPT, bool LEARNED>
 static cudaError_t launch_batched_t(const PolyParams& p, const float* x, const float* y,
                                     const int64_t* data_off, const int64_t* part_off,
                                     int32_t n_inst, int64_t n_items, int blocks_per_sm,
-                                    uint64_t seed, char* ws, ppl_is_result* out,
-                                    cudaStream_t s) {
+                                    uint64_t seed, const float* proposal, char* ws,
+                                    ppl_is_result* out, cudaStream_t s) {
   const BatchLayout l = batch_layout(n_items, n_inst);
   WsHeader* hdr = reinterpret_cast<WsHeader*>(ws + l.header);
   cudaError_t e = cudaMemsetAsync(ws + l.header, 0, 512, s);
@@ -163,38 +178,43 @@ static cudaError_t launch_batched_t(const PolyParams& p, const float* x, const f
   const size_t smem = trace_smem_bytes<PPT>() + kBatchChunk * sizeof(float2);
   static bool attr_set = false;
   if (!attr_set) {
-    e = cudaFuncSetAttribute(batched_kernel<PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+    e = cudaFuncSetAttribute(batched_kernel<PPT, LEARNED>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<PPT>, kTpb, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<PPT, LEARNED>, kTpb,
+                                                    smem);
   if (e != cudaSuccess) return e;
   const int bps = std::max(1, std::min(blocks_per_sm, std::max(1, per_sm)));
   const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(n_items, (int64_t)num_sms() * bps));
-  batched_kernel<PPT><<<(unsigned)grid, kTpb, smem, s>>>(
+  batched_kernel<PPT, LEARNED><<<(unsigned)grid, kTpb, smem, s>>>(
       p, x, y, data_off, part_off, reinterpret_cast<const BatchItem*>(ws + l.items), n_items,
       reinterpret_cast<const int32_t*>(ws + l.first), reinterpret_cast<int32_t*>(ws + l.count),
-      seed, hdr, reinterpret_cast<DegPartial*>(ws + l.parts), out);
+      seed, proposal, hdr, reinterpret_cast<DegPartial*>(ws + l.parts), out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_batched(const PolyParams& p, const float* x, const float* y,
                            const int64_t* data_off, const int64_t* part_off, int32_t n_inst,
-                           int64_t n_items, int ppt, int blocks_per_sm, uint64_t seed, char* ws,
-                           ppl_is_result* out, cudaStream_t s) {
+                           int64_t n_items, int ppt, int blocks_per_sm, uint64_t seed,
+                           const float* proposal, char* ws, ppl_is_result* out, cudaStream_t s) {
+#define PPL_BATCHED_CASE(P)                                                                   \
+  case P:                                                                                     \
+    return proposal ? launch_batched_t<P, true>(p, x, y, data_off, part_off, n_inst, n_items, \
+                                                blocks_per_sm, seed, proposal, ws, out, s)    \
+                    : launch_batched_t<P, false>(p, x, y, data_off, part_off, n_inst,         \
+                                                 n_items, blocks_per_sm, seed, nullptr, ws,   \
+                                                 out, s);
   switch (ppt) {
-    case 1: return launch_batched_t<1>(p, x, y, data_off, part_off, n_inst, n_items,
-                                       blocks_per_sm, seed, ws, out, s);
-    case 2: return launch_batched_t<2>(p, x, y, data_off, part_off, n_inst, n_items,
-                                       blocks_per_sm, seed, ws, out, s);
-    case 4: return launch_batched_t<4>(p, x, y, data_off, part_off, n_inst, n_items,
-                                       blocks_per_sm, seed, ws, out, s);
-    case 8: return launch_batched_t<8>(p, x, y, data_off, part_off, n_inst, n_items,
-                                       blocks_per_sm, seed, ws, out, s);
+    PPL_BATCHED_CASE(1)
+    PPL_BATCHED_CASE(2)
+    PPL_BATCHED_CASE(4)
+    PPL_BATCHED_CASE(8)
     default: return cudaErrorInvalidValue;
   }
+#undef PPL_BATCHED_CASE
 }
 
 // Host plan: items sorted heaviest first, per-instance first item and count.
@@ -329,7 +349,28 @@ ppl_status ppl_infer_is_batched(const ppl_model* model, const float* x, const fl
   if (ws_bytes < batch_layout(plan->n_items, n_inst).total) return PPL_EINVAL;
   const cudaError_t e =
       launch_batched(p, x, y, data_off, part_off, n_inst, plan->n_items, plan->ppt,
-                     plan->blocks_per_sm, seed, static_cast<char*>(ws), out_dev,
+                     plan->blocks_per_sm, seed, nullptr, static_cast<char*>(ws), out_dev,
+                     (cudaStream_t)stream);
+  return e == cudaSuccess ? PPL_OK : PPL_ECUDA;
+}
+
+ppl_status ppl_infer_is_learned(const ppl_model* model, const float* x, const float* y,
+                                const int64_t* data_off, const int64_t* part_off,
+                                int32_t n_inst, uint64_t seed, const ppl_batch_plan* plan,
+                                const float* proposal, ppl_is_result* out_dev, void* ws,
+                                size_t ws_bytes, ppl_stream stream) {
+  PolyParams p;
+  if (poly_params_b(model, &p) != PPL_OK || !(model->prior_sigma > 0.0f)) return PPL_EINVAL;
+  int slots = 0;
+  for (int k = 0; k < p.n_deg; ++k) slots += p.min_deg + k + p.coef_offset;
+  if (slots > kMaxSlots) return PPL_EINVAL;
+  if (!plan || !x || !y || !data_off || !part_off || !out_dev || !ws || !proposal)
+    return PPL_EINVAL;
+  if (plan->n_inst != n_inst || !valid_ppt(plan->ppt)) return PPL_EINVAL;
+  if (ws_bytes < batch_layout(plan->n_items, n_inst).total) return PPL_EINVAL;
+  const cudaError_t e =
+      launch_batched(p, x, y, data_off, part_off, n_inst, plan->n_items, plan->ppt,
+                     plan->blocks_per_sm, seed, proposal, static_cast<char*>(ws), out_dev,
                      (cudaStream_t)stream);
   return e == cudaSuccess ? PPL_OK : PPL_ECUDA;
 }

@@ -89,8 +89,8 @@ __global__ void __launch_bounds__(kTpb) poly_trace_kernel(
   __syncthreads();
   int nan = 0;
   for (int64_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
-    trace_group<PPT>(p, xs, ys, L, chunk, resident, sdata, N, g * group, seed, instance, lw_out,
-                     rec_out, ts, gout);
+    trace_group<PPT>(PriorDraw{p, seed, instance}, p, xs, ys, L, chunk, resident, sdata, N,
+                     g * group, lw_out, rec_out, ts, gout);
     if (tid < kMaxDegrees) deg_merge(run[tid], gout[tid]);
     if (tid == 0) nan |= ts.nan;
   }

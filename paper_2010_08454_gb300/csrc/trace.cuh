@@ -23,6 +23,7 @@ template <int PPT>
 struct TraceSmem {
   float c[kTpb * PPT * kCStride];
   float lw[kTpb * PPT];
+  float corr[kTpb * PPT];  // log p - log q of a trace drawn from a proposal (0 under the prior)
   int idx[kTpb * PPT];
   int wcount[PPT][kTpb / 32][kMaxDegrees];
   int wbase[PPT][kTpb / 32][kMaxDegrees];
@@ -95,28 +96,39 @@ __device__ __forceinline__ void accumulate_dispatch(int nc, const float2* sdata,
   }
 }
 
+// Draw policy of the prior (§3.4 `sample` from the model's own distributions):
+// log-weight correction 0.
+struct PriorDraw {
+  PolyParams p;
+  uint64_t seed;
+  uint32_t instance;
+  __device__ __forceinline__ int operator()(uint32_t i, float (&c)[kMaxCoef], float& corr) const {
+    corr = 0.0f;
+    return poly_draw(p, seed, instance, i, c);
+  }
+};
+
 // Runs traces [base, base + kTpb * PPT) of an instance with N traces and reduces
 // them into out[0..3] (per-degree partials).  Data: L points at xs, ys; when
 // `resident` the caller has staged all of them in sdata, otherwise they
 // stream through sdata in chunks of `chunk`.  lw_out / rec_out (optional) are
 // indexed by trace index.  Every thread of the block must call it.
-template <int PPT>
-__device__ __forceinline__ void trace_group(const PolyParams& p, const float* __restrict__ xs,
+template <int PPT, class Draw>
+__device__ __forceinline__ void trace_group(const Draw& draw, const PolyParams& p, const float* __restrict__ xs,
                                             const float* __restrict__ ys, int64_t L, int chunk,
                                             bool resident, float2* sdata, int64_t N,
-                                            int64_t base, uint64_t seed, uint32_t instance,
-                                            float* __restrict__ lw_out,
+                                            int64_t base, float* __restrict__ lw_out,
                                             ppl_poly_particle* __restrict__ rec_out,
                                             TraceSmem<PPT>& ts, DegPartial (&out)[kMaxDegrees]) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
   // A. draw, write the records, rank every trace within its degree
-  float c[PPT][kMaxCoef];
+  float c[PPT][kMaxCoef], corr[PPT];
   int d[PPT], rank[PPT];
 #pragma unroll
   for (int q = 0; q < PPT; ++q) {
     const int64_t i = base + (int64_t)q * kTpb + tid;
-    const int n = poly_draw(p, seed, instance, (uint32_t)(i < N ? i : 0), c[q]);
+    const int n = draw((uint32_t)(i < N ? i : 0), c[q], corr[q]);
     d[q] = (i < N) ? n - p.min_deg : -1;
     if (i < N && rec_out) {
       float4* dst = reinterpret_cast<float4*>(rec_out + i);
@@ -162,6 +174,7 @@ __device__ __forceinline__ void trace_group(const PolyParams& p, const float* __
     const int slot = ts.wbase[q][warp][d[q]] + rank[q];
 #pragma unroll
     for (int k = 0; k < kMaxCoef; ++k) ts.c[slot * kCStride + k] = c[q][k];
+    ts.corr[slot] = corr[q];
     ts.idx[slot] = (int)(base + (int64_t)q * kTpb + tid);
   }
   __syncthreads();
@@ -201,7 +214,7 @@ __device__ __forceinline__ void trace_group(const PolyParams& p, const float* __
 #pragma unroll
   for (int j = 0; j < PPT; ++j)
     if (slot[j] < n_valid) {
-      const float lw = ss[j] * p.neg_half_inv_var;
+      const float lw = ss[j] * p.neg_half_inv_var + ts.corr[slot[j]];
       ts.lw[slot[j]] = lw;
       if (lw_out) lw_out[ts.idx[slot[j]]] = lw;
     }

@@ -1,0 +1,167 @@
+"""Parity of the learned-proposal path with its oracle: features, the BF16
+network, the gradient of -log q, importance sampling under a given proposal;
+the prior special case; training; and the gain over the prior proposal."""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import load_ppl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ppl():
+    return load_ppl()
+
+
+@pytest.fixture(scope="module")
+def mlp(orc):
+    from oracle import mlp
+    return mlp
+
+
+def _t(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_features_bit_exact(ppl, mlp):
+    d = synth.prior_datasets(200, 32, 3)
+    feat = ppl.ppl_proposal_features(_t(d["x"]), _t(d["y"])).float().cpu().numpy()
+    for b in range(200):
+        assert np.array_equal(feat[b], mlp.features(d["x"][b], d["y"][b])), b
+
+
+def test_network_forward_matches_oracle(ppl, mlp, orc):
+    W = synth.mlp_weights(7)
+    d = synth.prior_datasets(300, 32, 4)
+    out = ppl.ppl_proposal_forward(ppl.poly_model(), ppl.pack_params(W), _t(d["x"]),
+                                   _t(d["y"])).cpu().numpy()
+    ref = np.stack([mlp.forward(W, mlp.features(d["x"][b], d["y"][b]))[0] for b in range(300)])
+    scale = np.abs(ref).max()
+    err = np.abs(out - ref)
+    # FP32 accumulation and BF16 activations: rare one-ulp BF16 flips in h1/h2
+    assert np.median(err) < 1e-4 * scale and err.max() < 2e-2 * scale, (np.median(err), err.max())
+
+
+def test_gradient_matches_oracle_backprop(ppl, mlp, orc):
+    W = synth.mlp_weights(8, bias_scale=0.3)
+    m = orc.poly_model()
+    B = 512
+    grad, loss = ppl.ppl_proposal_grad(ppl.poly_model(), ppl.pack_params(W), 100, B, 21)
+    pairs = [mlp.forward_sim(m, 21, 100 + p) for p in range(B)]
+    feats = np.stack([mlp.features(x, y) for x, y, _, _ in pairs])
+    n = np.array([p[2] for p in pairs])
+    c = np.stack([p[3] for p in pairs])
+    ref_loss, g = mlp.loss_grad(m, W, feats, n, c)
+    assert float(loss.item()) / B == pytest.approx(ref_loss, rel=2e-3)
+    flat = grad.cpu().numpy()
+    off = 0
+    for gi in g:
+        got = flat[off:off + gi.size].reshape(gi.shape)
+        off += gi.size
+        rel = np.linalg.norm(got - gi) / (np.linalg.norm(gi) + 1e-30)
+        assert rel < 3e-2, rel
+
+
+def test_forward_simulation_matches_oracle(ppl, mlp, orc):
+    import torch
+    m = orc.poly_model()
+    # the gradient call draws the pairs; compare their degrees through the loss of
+    # a network whose logits select degree 2: -log q depends on n only through
+    # the coefficient slots, so compare draws directly via the features instead
+    d_pairs = [mlp.forward_sim(m, 5, p) for p in range(64)]
+    x = np.stack([p[0] for p in d_pairs])
+    y = np.stack([p[1] for p in d_pairs])
+    feat = ppl.ppl_proposal_features(_t(x), _t(y)).float().cpu().numpy()
+    ref = np.stack([mlp.features(a, b) for a, b in zip(x, y)])
+    assert np.array_equal(feat, ref)
+
+
+def _uniform_batch(n_sets, N, L=32):
+    data_off = np.arange(n_sets + 1, dtype=np.int64) * L
+    part_off = np.arange(n_sets + 1, dtype=np.int64) * N
+    return data_off, part_off
+
+
+def test_prior_equal_proposal_reproduces_prior_batched_run(ppl):
+    d = synth.prior_datasets(24, 32, 9)
+    doff, poff = _uniform_batch(24, 5000)
+    model = ppl.poly_model()
+    ws = ppl.batched_workspace(doff, poff)
+    plan = ppl.ppl_batched_prepare(model, doff, poff, 4, 2, ws)
+    x, y = _t(d["x"].reshape(-1)), _t(d["y"].reshape(-1))
+    out_p = ppl.batch_results_tensor(24)
+    ppl.ppl_infer_is_batched(model, x, y, _t(doff), _t(poff), 3, plan, out_p, ws)
+    out_l = ppl.batch_results_tensor(24)
+    prop = _t(np.zeros((24, 48), dtype=np.float32))
+    ppl.ppl_infer_is_learned(model, x, y, _t(doff), _t(poff), 3, plan, prop, out_l, ws)
+    import torch
+    assert torch.equal(out_p, out_l)
+
+
+def test_learned_is_matches_oracle_under_a_given_proposal(ppl, mlp, orc):
+    W = synth.mlp_weights(11, bias_scale=0.3)
+    d = synth.prior_datasets(16, 32, 12)
+    m = orc.poly_model()
+    outs = np.stack([mlp.forward(W, mlp.features(d["x"][b], d["y"][b]))[0] for b in range(16)])
+    prop = outs.astype(np.float32)
+    N = 20000
+    doff, poff = _uniform_batch(16, N)
+    model = ppl.poly_model()
+    ws = ppl.batched_workspace(doff, poff)
+    plan = ppl.ppl_batched_prepare(model, doff, poff, 4, 2, ws)
+    res = ppl.read_batch_results(ppl.ppl_infer_is_learned(
+        model, _t(d["x"].reshape(-1)), _t(d["y"].reshape(-1)), _t(doff), _t(poff), 6, plan,
+        _t(prop), ppl.batch_results_tensor(16), ws), 16)
+    for b in range(16):
+        lw, n, c = mlp.learned_is(m, prop[b].astype(np.float64), d["x"][b], d["y"][b], N, 6,
+                                  instance=b)
+        ref = orc.posterior_poly(m, lw, n, c)
+        r = res[b]
+        tol = 1e-3 + 2.0 ** -21 * abs(ref["max_lw"])
+        assert r["status"] == 0
+        assert abs(r["log_z"] - ref["log_z"]) <= tol, (b, r["log_z"], ref["log_z"])
+        assert np.allclose(r["p_n"], ref["p_n"], rtol=1e-3, atol=1e-9), b
+
+
+def test_training_reduces_loss_and_beats_the_prior(ppl, orc):
+    import torch
+    model = ppl.poly_model()
+    W = synth.mlp_weights(1)
+    params = ppl.pack_params(W)
+    am = torch.zeros_like(params)
+    av = torch.zeros_like(params)
+    n_pairs, batch, epochs = 1 << 19, 1024, 2
+    losses = torch.zeros(epochs * (n_pairs // batch), dtype=torch.float64, device="cuda")
+    ppl.ppl_proposal_train(model, params, am, av, n_pairs, batch, epochs, 99, 1e-3, losses)
+    lc = losses.cpu().numpy() / batch
+    assert np.all(np.isfinite(lc))
+    assert lc[-20:].mean() < lc[:20].mean() - 5.0, (lc[:20].mean(), lc[-20:].mean())
+    # held-out data sets from the model: learned proposal vs prior at equal particles
+    n_sets, N = 32, 1 << 14
+    d = synth.prior_datasets(n_sets, 32, 4242)
+    x, y = _t(d["x"]), _t(d["y"])
+    prop = ppl.ppl_proposal_forward(model, params, x, y)
+    doff, poff = _uniform_batch(n_sets, N)
+    ws = ppl.batched_workspace(doff, poff)
+    plan = ppl.ppl_batched_prepare(model, doff, poff, 4, 2, ws)
+    xf, yf = x.reshape(-1).contiguous(), y.reshape(-1).contiguous()
+    learned = ppl.read_batch_results(ppl.ppl_infer_is_learned(
+        model, xf, yf, _t(doff), _t(poff), 7, plan, prop, ppl.batch_results_tensor(n_sets), ws),
+        n_sets)
+    prior = ppl.read_batch_results(ppl.ppl_infer_is_batched(
+        model, xf, yf, _t(doff), _t(poff), 7, plan, ppl.batch_results_tensor(n_sets), ws), n_sets)
+    om = orc.poly_model()
+    err_l, err_p, ess_l, ess_p = [], [], [], []
+    for b in range(n_sets):
+        ex = orc.poly_exact(om, d["x"][b], d["y"][b])["log_z"]
+        err_l.append(abs(learned[b]["log_z"] - ex))
+        err_p.append(abs(prior[b]["log_z"] - ex))
+        ess_l.append(learned[b]["ess"])
+        ess_p.append(prior[b]["ess"])
+    assert np.median(ess_l) > 10 * np.median(ess_p), (np.median(ess_l), np.median(ess_p))
+    assert np.mean(np.array(err_l) < 0.05) > np.mean(np.array(err_p) < 0.05)
