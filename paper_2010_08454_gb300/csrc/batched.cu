@@ -33,10 +33,12 @@ struct BatchItem {
 
 // Workspace layout of a prepared plan (offsets from the workspace base).
 struct BatchLayout {
-  size_t header, items, first, count_tmpl, count, parts, total;
+  size_t header, items, first, count_tmpl, count, inst_max, parts, total;
 };
 
 static size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+constexpr int kWarpParts = (kTpb / 32) * kMaxDegrees;  // partials one tile leaves
 
 static BatchLayout batch_layout(int64_t n_items, int32_t n_inst) {
   BatchLayout l;
@@ -51,8 +53,10 @@ static BatchLayout batch_layout(int64_t n_items, int32_t n_inst) {
   off += align256((size_t)n_inst * sizeof(int32_t));
   l.count = off;
   off += align256((size_t)n_inst * sizeof(int32_t));
+  l.inst_max = off;
+  off += align256((size_t)n_inst * kMaxDegrees * sizeof(int32_t));
   l.parts = off;
-  off += align256((size_t)n_items * kMaxDegrees * sizeof(DegPartial));
+  off += align256((size_t)n_items * kWarpParts * sizeof(DegPartial));
   l.total = off;
   return l;
 }
@@ -60,12 +64,12 @@ static BatchLayout batch_layout(int64_t n_items, int32_t n_inst) {
 constexpr int kBatchChunk = 4096;  // data points staged in shared memory at a time
 
 template <int PPT, bool LEARNED>
-__global__ void __launch_bounds__(kTpb) batched_kernel(
+__global__ void __launch_bounds__(kTpb, PPT >= 8 ? 2 : 3) batched_kernel(
     PolyParams p, const float* __restrict__ xs, const float* __restrict__ ys,
     const int64_t* __restrict__ data_off, const int64_t* __restrict__ part_off,
     const BatchItem* __restrict__ items, int64_t n_items, const int32_t* __restrict__ first,
-    int32_t* count, uint64_t seed, const float* __restrict__ proposal, WsHeader* hdr,
-    DegPartial* parts, ppl_is_result* out) {
+    int32_t* count, uint64_t seed, const float* __restrict__ proposal, int* inst_max,
+    WsHeader* hdr, DegPartial* parts, ppl_is_result* out) {
   extern __shared__ __align__(16) unsigned char smem[];
   TraceSmem<PPT>& ts = *reinterpret_cast<TraceSmem<PPT>*>(smem);
   float2* sdata = reinterpret_cast<float2*>(smem + trace_smem_bytes<PPT>());
@@ -75,6 +79,7 @@ __global__ void __launch_bounds__(kTpb) batched_kernel(
   __shared__ bool last_sh;
   __shared__ ProposalSmem prop;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  reset_warp_partials(ts);
   int cur = -1;      // instance whose data is staged
   int cur_prop = -1;  // instance whose proposal is loaded
   while (true) {
@@ -94,6 +99,13 @@ __global__ void __launch_bounds__(kTpb) batched_kernel(
       cur = -1;  // the chunks overwrite the staged data
     }
     const int64_t tbase = (int64_t)items[it].tile * kTpb * PPT;
+    // maxima already reached by this instance's finished items bound the final
+    // maxima from below: traces far beneath them are skipped (trace_group)
+    if (tid < kMaxDegrees) {
+      const int k = ld_volatile_i32(inst_max + (int64_t)b * kMaxDegrees + tid);
+      ts.ext_max[tid] = (k == 0) ? -INFINITY : key_float(k);
+    }
+    __syncthreads();
     if (LEARNED) {
       if (b != cur_prop) {
         __syncthreads();
@@ -102,14 +114,32 @@ __global__ void __launch_bounds__(kTpb) batched_kernel(
         cur_prop = b;
       }
       trace_group<PPT>(LearnedDraw{p, seed, (uint32_t)b, &prop}, p, xs + d0, ys + d0, L,
-                       kBatchChunk, resident, sdata, N, tbase, nullptr, nullptr, ts, gout);
+                       kBatchChunk, resident, sdata, N, tbase, nullptr, nullptr, ts);
     } else {
       trace_group<PPT>(PriorDraw{p, seed, (uint32_t)b}, p, xs + d0, ys + d0, L, kBatchChunk,
-                       resident, sdata, N, tbase, nullptr, nullptr, ts, gout);
+                       resident, sdata, N, tbase, nullptr, nullptr, ts);
     }
-    if (tid < kMaxDegrees) parts[it * kMaxDegrees + tid] = gout[tid];
+    // each warp leaves its per-degree partials of this tile in the tile's slot
+    // and raises the instance's running maxima; no block-level merge per tile
+    {
+      const int64_t slot0 = ((int64_t)first[b] + items[it].tile) * kWarpParts + warp * kMaxDegrees;
+      __syncwarp();
+      if (lane < kMaxDegrees * 4) {
+        const float4* src = reinterpret_cast<const float4*>(&ts.wrun[warp * kMaxDegrees]);
+        reinterpret_cast<float4*>(parts + slot0)[lane] = src[lane];
+      }
+      if (lane < kMaxDegrees) {
+        const float m = ts.wrun[warp * kMaxDegrees + lane].m;
+        if (m > -INFINITY) atomicMax(inst_max + (int64_t)b * kMaxDegrees + lane, float_key(m));
+      }
+      __syncwarp();
+      if (lane < kMaxDegrees) deg_empty(ts.wrun[warp * kMaxDegrees + lane]);
+      if (tid < kMaxDegrees) ts.ext_max[tid] = -INFINITY;
+    }
     if (tid == 0 && ts.nan) record_status(&hdr->status, PPL_ENAN);
-    // the last item of the instance merges the instance's partials
+    // the last item of the instance merges the instance's partials; the
+    // barrier and thread 0's fence order every warp's partial writes before
+    // the count (fences are cumulative)
     __syncthreads();
     if (tid == 0) {
       __threadfence();
@@ -120,11 +150,12 @@ __global__ void __launch_bounds__(kTpb) batched_kernel(
       __threadfence();
       const int64_t i0 = first[b];
       const int64_t ni = (N + (int64_t)kTpb * PPT - 1) / ((int64_t)kTpb * PPT);
+      const int64_t np = ni * (kTpb / 32);  // (tile, warp) partials per degree
       if (warp < kMaxDegrees) {
         DegPartial a;
         deg_empty(a);
-        for (int64_t j = lane; j < ni; j += 32) {
-          const DegPartial q = ld_partial_cg(parts + (i0 + j) * kMaxDegrees + warp);
+        for (int64_t j = lane; j < np; j += 32) {
+          const DegPartial q = ld_partial_cg(parts + (i0 * (kTpb / 32) + j) * kMaxDegrees + warp);
           deg_merge(a, q);
         }
 #pragma unroll
@@ -134,8 +165,8 @@ __global__ void __launch_bounds__(kTpb) batched_kernel(
         }
         double s = 0.0, s2 = 0.0;
         if (a.m != -INFINITY) {
-          for (int64_t j = lane; j < ni; j += 32) {
-            const DegPartial q = ld_partial_cg(parts + (i0 + j) * kMaxDegrees + warp);
+          for (int64_t j = lane; j < np; j += 32) {
+            const DegPartial q = ld_partial_cg(parts + (i0 * (kTpb / 32) + j) * kMaxDegrees + warp);
             if (q.m == -INFINITY) continue;
             const double e = (double)expf(q.m - a.m);
             s += (double)q.S * e;
@@ -175,6 +206,8 @@ static cudaError_t launch_batched_t(const PolyParams& p, const float* x, const f
   e = cudaMemcpyAsync(ws + l.count, ws + l.count_tmpl, (size_t)n_inst * sizeof(int32_t),
                       cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(ws + l.inst_max, 0, (size_t)n_inst * kMaxDegrees * sizeof(int32_t), s);
+  if (e != cudaSuccess) return e;
   const size_t smem = trace_smem_bytes<PPT>() + kBatchChunk * sizeof(float2);
   static bool attr_set = false;
   if (!attr_set) {
@@ -192,7 +225,8 @@ static cudaError_t launch_batched_t(const PolyParams& p, const float* x, const f
   batched_kernel<PPT, LEARNED><<<(unsigned)grid, kTpb, smem, s>>>(
       p, x, y, data_off, part_off, reinterpret_cast<const BatchItem*>(ws + l.items), n_items,
       reinterpret_cast<const int32_t*>(ws + l.first), reinterpret_cast<int32_t*>(ws + l.count),
-      seed, proposal, hdr, reinterpret_cast<DegPartial*>(ws + l.parts), out);
+      seed, proposal, reinterpret_cast<int*>(ws + l.inst_max), hdr,
+      reinterpret_cast<DegPartial*>(ws + l.parts), out);
   return cudaGetLastError();
 }
 
@@ -217,7 +251,12 @@ cudaError_t launch_batched(const PolyParams& p, const float* x, const float* y,
 #undef PPL_BATCHED_CASE
 }
 
-// Host plan: items sorted heaviest first, per-instance first item and count.
+// Host plan.  Items are issued in rounds: round r holds tile r of every
+// instance with more than r tiles, heaviest (longest data) first.  An
+// instance's first tile thus finishes early and its maxima let the later
+// tiles skip negligible traces; within a round the heaviest-first order keeps
+// the blocks finishing together.  first[b] is instance b's base among the
+// per-tile partial slots (contiguous per instance); count[b] its tile count.
 static int64_t build_plan(const int64_t* data_off, const int64_t* part_off, int32_t n_inst,
                           int ppt, std::vector<BatchItem>* items, std::vector<int32_t>* first,
                           std::vector<int32_t>* count, int64_t* max_len, double* work) {
@@ -232,16 +271,21 @@ static int64_t build_plan(const int64_t* data_off, const int64_t* part_off, int3
   count->assign(n_inst, 0);
   *max_len = 0;
   *work = 0.0;
-  for (int32_t b : order) {
+  int64_t slots = 0, max_tiles = 0;
+  for (int32_t b = 0; b < n_inst; ++b) {
     const int64_t L = data_off[b + 1] - data_off[b];
     const int64_t N = part_off[b + 1] - part_off[b];
     const int64_t tiles = (N + tile - 1) / tile;
-    (*first)[b] = (int32_t)items->size();
+    (*first)[b] = (int32_t)slots;
     (*count)[b] = (int32_t)tiles;
-    for (int64_t t = 0; t < tiles; ++t) items->push_back(BatchItem{b, (int32_t)t});
+    slots += tiles;
+    max_tiles = std::max(max_tiles, tiles);
     *max_len = std::max(*max_len, L);
     *work += (double)N * (double)L;
   }
+  for (int64_t r = 0; r < max_tiles; ++r)
+    for (int32_t b : order)
+      if (r < (*count)[b]) items->push_back(BatchItem{b, (int32_t)r});
   return (int64_t)items->size();
 }
 

@@ -86,6 +86,7 @@ __device__ __forceinline__ int32_t ld_volatile_i32(const int32_t* p) {
 // it returns true in exactly one block, after all partials are visible.
 __device__ __forceinline__ bool elect_last_block(uint32_t* ticket) {
   __shared__ bool last;
+  __threadfence();  // every thread's partial writes are device-visible before the ticket
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();

@@ -70,7 +70,7 @@ __device__ __forceinline__ void finalize_partials(const DegPartial* parts, int G
 // last block merges the blocks' partials into the summary.
 // ---------------------------------------------------------------------------
 template <int PPT>
-__global__ void __launch_bounds__(kTpb) poly_trace_kernel(
+__global__ void __launch_bounds__(kTpb, 3) poly_trace_kernel(
     PolyParams p, const float* __restrict__ xs, const float* __restrict__ ys, int64_t L,
     int64_t N, uint64_t seed, uint32_t instance, int chunk, float* __restrict__ lw_out,
     ppl_poly_particle* __restrict__ rec_out, WsHeader* hdr, DegPartial* parts,
@@ -78,23 +78,22 @@ __global__ void __launch_bounds__(kTpb) poly_trace_kernel(
   extern __shared__ __align__(16) unsigned char smem[];
   TraceSmem<PPT>& ts = *reinterpret_cast<TraceSmem<PPT>*>(smem);
   float2* sdata = reinterpret_cast<float2*>(smem + trace_smem_bytes<PPT>());
-  __shared__ DegPartial run[kMaxDegrees], gout[kMaxDegrees];
+  __shared__ DegPartial run[kMaxDegrees];
   const int tid = threadIdx.x;
   const int64_t group = (int64_t)kTpb * PPT;
   const int64_t n_groups = (N + group - 1) / group;
   const bool resident = L <= chunk;
-  if (tid < kMaxDegrees) deg_empty(run[tid]);
+  reset_warp_partials(ts);
   if (resident)
     for (int l = tid; l < L; l += kTpb) sdata[l] = make_float2(xs[l], ys[l]);
   __syncthreads();
   int nan = 0;
   for (int64_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
     trace_group<PPT>(PriorDraw{p, seed, instance}, p, xs, ys, L, chunk, resident, sdata, N,
-                     g * group, lw_out, rec_out, ts, gout);
-    if (tid < kMaxDegrees) deg_merge(run[tid], gout[tid]);
+                     g * group, lw_out, rec_out, ts);
     if (tid == 0) nan |= ts.nan;
   }
-  __syncthreads();
+  merge_warp_partials(ts, run);
   if (tid < kMaxDegrees) parts[blockIdx.x * kMaxDegrees + tid] = run[tid];
   if (tid == 0 && nan) record_status(&hdr->status, PPL_ENAN);
   if (elect_last_block(&hdr->ticket[0]))

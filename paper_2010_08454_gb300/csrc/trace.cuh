@@ -16,20 +16,63 @@
 
 namespace ppl {
 
-constexpr int kCStride = 7;  // shared-memory stride of a trace's coefficients (odd: no bank conflicts)
+
+constexpr int kCStride = 7;
+constexpr float kSkipNats = 50.0f;  // traces this far below their degree's running maximum are skipped
+constexpr int kSerialMerges = 4;    // up to this many traces a warp merges one at a time  // shared-memory stride of a trace's coefficients (odd: no bank conflicts)
 
 // Shared memory of one group of kTpb * PPT traces.
 template <int PPT>
 struct TraceSmem {
+  // coefficients of a trace at [slot * 7, slot * 7 + 6); [slot * 7 + 6] holds its
+  // log p - log q when it was drawn from a proposal (0 under the prior)
   float c[kTpb * PPT * kCStride];
-  float lw[kTpb * PPT];
-  float corr[kTpb * PPT];  // log p - log q of a trace drawn from a proposal (0 under the prior)
   int idx[kTpb * PPT];
   int wcount[PPT][kTpb / 32][kMaxDegrees];
   int wbase[PPT][kTpb / 32][kMaxDegrees];
   int off[kMaxDegrees + 1];
   int nan;
+  DegPartial wrun[(kTpb / 32) * kMaxDegrees];  // each warp's running per-degree partials
+  float ext_max[kMaxDegrees];  // known lower bounds of the final per-degree maxima (or -inf)
 };
+
+// Float <-> int keys that order like the floats (for atomicMax on maxima).
+__device__ __forceinline__ int float_key(float f) {
+  const int b = __float_as_int(f);
+  return b >= 0 ? b : (b ^ 0x7fffffff);
+}
+__device__ __forceinline__ float key_float(int k) {
+  return __int_as_float(k >= 0 ? k : (k ^ 0x7fffffff));
+}
+
+// Clear the warps' running partials (before the first group).
+template <int PPT>
+__device__ __forceinline__ void reset_warp_partials(TraceSmem<PPT>& ts) {
+  for (int e = threadIdx.x; e < (kTpb / 32) * kMaxDegrees; e += blockDim.x) deg_empty(ts.wrun[e]);
+  if (threadIdx.x < kMaxDegrees) ts.ext_max[threadIdx.x] = -INFINITY;
+}
+
+// Merge the warps' running partials into out[0..3] and clear them; every
+// thread of the block must call it.  Warp 0 holds partial (warp w, degree d)
+// in lane 8 d + w and merges by a three-round shuffle tree.
+template <int PPT>
+__device__ __forceinline__ void merge_warp_partials(TraceSmem<PPT>& ts,
+                                                    DegPartial (&out)[kMaxDegrees]) {
+  static_assert(kTpb / 32 == 8 && kMaxDegrees == 4, "one lane per (warp, degree)");
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x, w = lane & 7, d = lane >> 3;
+    DegPartial r = ts.wrun[w * kMaxDegrees + d];
+    deg_empty(ts.wrun[w * kMaxDegrees + d]);
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const DegPartial other = deg_shfl_xor(r, o);
+      deg_merge(r, other);
+    }
+    if (w == 0) out[d] = r;
+  }
+  __syncthreads();
+}
 
 template <int PPT>
 __host__ __device__ constexpr size_t trace_smem_bytes() {
@@ -108,8 +151,8 @@ struct PriorDraw {
   }
 };
 
-// Runs traces [base, base + kTpb * PPT) of an instance with N traces and reduces
-// them into out[0..3] (per-degree partials).  Data: L points at xs, ys; when
+// Runs traces [base, base + kTpb * PPT) of an instance with N traces and merges
+// them into the warps' running per-degree partials (ts.wrun).  Data: L points at xs, ys; when
 // `resident` the caller has staged all of them in sdata, otherwise they
 // stream through sdata in chunks of `chunk`.  lw_out / rec_out (optional) are
 // indexed by trace index.  Every thread of the block must call it.
@@ -119,7 +162,7 @@ __device__ __forceinline__ void trace_group(const Draw& draw, const PolyParams& 
                                             bool resident, float2* sdata, int64_t N,
                                             int64_t base, float* __restrict__ lw_out,
                                             ppl_poly_particle* __restrict__ rec_out,
-                                            TraceSmem<PPT>& ts, DegPartial (&out)[kMaxDegrees]) {
+                                            TraceSmem<PPT>& ts) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
   // A. draw, write the records, rank every trace within its degree
@@ -174,7 +217,7 @@ __device__ __forceinline__ void trace_group(const Draw& draw, const PolyParams& 
     const int slot = ts.wbase[q][warp][d[q]] + rank[q];
 #pragma unroll
     for (int k = 0; k < kMaxCoef; ++k) ts.c[slot * kCStride + k] = c[q][k];
-    ts.corr[slot] = corr[q];
+    ts.c[slot * kCStride + kMaxCoef] = corr[q];
     ts.idx[slot] = (int)(base + (int64_t)q * kTpb + tid);
   }
   __syncthreads();
@@ -211,91 +254,153 @@ __device__ __forceinline__ void trace_group(const Draw& draw, const PolyParams& 
       if (active) accumulate_dispatch<PPT>(nc, sdata, len, c, ss, comp);
     }
   }
+  // C. each warp folds its traces into its running per-degree partials.  A
+  // trace more than kSkipNats below the running maximum of its degree carries
+  // a weight below e^-50 of that maximum: even 2^31 such traces change no sum
+  // by more than 4e-13 relative (below FP32 resolution), and the maximum only
+  // grows, so such traces are skipped.  The rest are merged: one at a time by
+  // lane 0 when there are few, otherwise by a warp reduction per degree.
+  float lw[PPT];
+  int deg[PPT];
+  float thr[kMaxDegrees];
 #pragma unroll
-  for (int j = 0; j < PPT; ++j)
+  for (int k = 0; k < kMaxDegrees; ++k)
+    thr[k] = fmaxf(ts.wrun[warp * kMaxDegrees + k].m, ts.ext_max[k]) - kSkipNats;
+  int ncand = 0, nan = 0;
+  unsigned cmask[PPT];
+#pragma unroll
+  for (int j = 0; j < PPT; ++j) {
+    deg[j] = -1;
+    lw[j] = -INFINITY;
+    bool cand = false;
     if (slot[j] < n_valid) {
-      const float lw = ss[j] * p.neg_half_inv_var + ts.corr[slot[j]];
-      ts.lw[slot[j]] = lw;
-      if (lw_out) lw_out[ts.idx[slot[j]]] = lw;
-    }
-  __syncthreads();
-
-  // C. one warp per degree bucket: best trace, then sums around it
-  if (warp < kMaxDegrees) {
-    const int k = warp, s0 = ts.off[k], s1 = ts.off[k + 1];
-    float m = -INFINITY;
-    int a = 0x7fffffff, as = -1, nan = 0;
-    for (int s = s0 + lane; s < s1; s += 32) {
-      const float v = ts.lw[s];
-      nan |= v != v;
-      if (v > m || (v == m && ts.idx[s] < a)) {
-        m = v;
-        a = ts.idx[s];
-        as = s;
-      }
-    }
+      lw[j] = ss[j] * p.neg_half_inv_var + ts.c[slot[j] * kCStride + kMaxCoef];
+      if (lw_out) lw_out[ts.idx[slot[j]]] = lw[j];
+      int dj = 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float om = __shfl_xor_sync(0xffffffffu, m, o);
-      const int oa = __shfl_xor_sync(0xffffffffu, a, o);
-      const int os = __shfl_xor_sync(0xffffffffu, as, o);
-      if (om > m || (om == m && oa < a)) {
-        m = om;
-        a = oa;
-        as = os;
+      for (int k = 1; k < kMaxDegrees; ++k)
+        if (slot[j] >= ts.off[k]) dj = k;
+      deg[j] = dj;
+      float t = thr[0];
+#pragma unroll
+      for (int k = 1; k < kMaxDegrees; ++k)
+        if (dj == k) t = thr[k];
+      cand = !(lw[j] <= t);  // NaN log-weights are candidates, so they are seen
+      nan |= lw[j] != lw[j];
+    }
+    cmask[j] = __ballot_sync(0xffffffffu, cand);
+    ncand += __popc(cmask[j]);
+  }
+  if (ncand > 0 && ncand <= kSerialMerges) {
+    // few candidates: lane 0 merges each as a one-trace partial
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      unsigned msk = cmask[j];
+      while (msk) {
+        const int src = __ffs(msk) - 1;
+        msk &= msk - 1;
+        const float v = __shfl_sync(0xffffffffu, lw[j], src);
+        const int dv = __shfl_sync(0xffffffffu, deg[j], src);
+        const int sv = __shfl_sync(0xffffffffu, slot[j], src);
+        if (lane == 0) {
+          DegPartial r;
+          deg_empty(r);
+          r.m = v;
+          r.arg = ts.idx[sv];
+          if (v > -INFINITY) {
+            r.S = 1.0f;
+            r.S2 = 1.0f;
+#pragma unroll
+            for (int k = 0; k < kMaxCoef; ++k) r.mean[k] = ts.c[sv * kCStride + k];
+          }
+          deg_merge(ts.wrun[warp * kMaxDegrees + dv], r);
+        }
       }
     }
-    nan = __any_sync(0xffffffffu, nan);
-    DegPartial r;
-    deg_empty(r);
-    r.m = m;
-    r.arg = a;
-    if (m > -INFINITY) {
+  } else if (ncand > kSerialMerges) {
+    int dlo = 0;
+#pragma unroll
+    for (int k = 1; k < kMaxDegrees; ++k)
+      if (warp * 32 * PPT >= ts.off[k]) dlo = k;
+    for (int dd = dlo; dd <= dlast; ++dd) {
+      float m = -INFINITY;
+      int a = 0x7fffffff, as = -1;
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) {
+        const bool cj = (cmask[j] >> lane) & 1u;
+        if (cj && deg[j] == dd) {
+          const int ij = ts.idx[slot[j]];
+          if (lw[j] > m || (lw[j] == m && ij < a)) {
+            m = lw[j];
+            a = ij;
+            as = slot[j];
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float om = __shfl_xor_sync(0xffffffffu, m, o);
+        const int oa = __shfl_xor_sync(0xffffffffu, a, o);
+        const int os = __shfl_xor_sync(0xffffffffu, as, o);
+        if (om > m || (om == m && oa < a)) {
+          m = om;
+          a = oa;
+          as = os;
+        }
+      }
+      if (!(m > -INFINITY)) continue;  // no finite candidate of this degree
       float ref[kMaxCoef];
 #pragma unroll
-      for (int j = 0; j < kMaxCoef; ++j) ref[j] = ts.c[as * kCStride + j];
+      for (int k = 0; k < kMaxCoef; ++k) ref[k] = ts.c[as * kCStride + k];
       float S = 0.0f, S2 = 0.0f, A[kMaxCoef], B[kMaxCoef];
 #pragma unroll
-      for (int j = 0; j < kMaxCoef; ++j) {
-        A[j] = 0.0f;
-        B[j] = 0.0f;
+      for (int k = 0; k < kMaxCoef; ++k) {
+        A[k] = 0.0f;
+        B[k] = 0.0f;
       }
-      for (int s = s0 + lane; s < s1; s += 32) {
-        const float v = ts.lw[s];
-        const float w = (v > -INFINITY) ? expf(v - m) : 0.0f;
+#pragma unroll
+      for (int j = 0; j < PPT; ++j) {
+        const bool cj = (cmask[j] >> lane) & 1u;
+        if (!cj || deg[j] != dd) continue;
+        const float w = (lw[j] > -INFINITY) ? expf(lw[j] - m) : 0.0f;
         S += w;
         S2 = fmaf(w, w, S2);
 #pragma unroll
-        for (int j = 0; j < kMaxCoef; ++j) {
-          const float dc = ts.c[s * kCStride + j] - ref[j];
+        for (int k = 0; k < kMaxCoef; ++k) {
+          const float dc = ts.c[slot[j] * kCStride + k] - ref[k];
           const float t = w * dc;
-          A[j] += t;
-          B[j] = fmaf(t, dc, B[j]);
+          A[k] += t;
+          B[k] = fmaf(t, dc, B[k]);
         }
       }
       S = warp_sum(S);
       S2 = warp_sum(S2);
 #pragma unroll
-      for (int j = 0; j < kMaxCoef; ++j) {
-        A[j] = warp_sum(A[j]);
-        B[j] = warp_sum(B[j]);
+      for (int k = 0; k < kMaxCoef; ++k) {
+        A[k] = warp_sum(A[k]);
+        B[k] = warp_sum(B[k]);
       }
-      r.S = S;
-      r.S2 = S2;
-      if (S > 0.0f) {
+      if (lane == 0) {
+        DegPartial r;
+        deg_empty(r);
+        r.m = m;
+        r.arg = a;
+        r.S = S;
+        r.S2 = S2;
+        if (S > 0.0f) {
 #pragma unroll
-        for (int j = 0; j < kMaxCoef; ++j) {
-          const float mean_shift = A[j] / S;
-          r.mean[j] = ref[j] + mean_shift;
-          r.M2[j] = fmaxf(B[j] - mean_shift * A[j], 0.0f);
+          for (int k = 0; k < kMaxCoef; ++k) {
+            const float sh = A[k] / S;
+            r.mean[k] = ref[k] + sh;
+            r.M2[k] = fmaxf(B[k] - sh * A[k], 0.0f);
+          }
         }
+        deg_merge(ts.wrun[warp * kMaxDegrees + dd], r);
       }
-    }
-    if (lane == 0) {
-      out[k] = r;
-      if (nan) ts.nan = 1;
     }
   }
+  nan = __any_sync(0xffffffffu, nan);
+  if (lane == 0 && nan) ts.nan = 1;
   __syncthreads();
 }
 
