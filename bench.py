@@ -38,7 +38,7 @@ UNIT = "traces/s"
 WORKLOAD = ("linefitting likelihood weighting, 2^24 particles x 256 points, degree "
             "uniform{2..5}, coefficients N(0,10^2), sigma 0.5; + log-sum-exp/ESS + posterior "
             "reduce + systematic resampling (64-bit fixed point) + gather of 32-byte records")
-KERNELS_PER_STEP = 5  # trace (posterior fused), max/LSE pass, scan, ancestors, gather
+KERNELS_PER_STEP = 5  # trace (posterior fused), scan, chunk bounds, ancestors, gather
 
 
 def parse():
@@ -399,6 +399,7 @@ def run_ours(args):
     parts_out = ppl.poly_particles(N, dev)
     anc = torch.empty(N, dtype=torch.int32, device=dev)
     res = ppl.result_tensor(dev)
+    max_lw = ppl.result_max_lw(res)
     ws = ppl.workspace(model, N, N_POINTS, dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
@@ -411,7 +412,7 @@ def run_ours(args):
         if ev:
             ev[1].record(stream)
             ev[2].record(stream)
-        ppl.ppl_resample(N, INFER_SEED, instance, 0, lw=lw, ancestors=anc, ws=ws)
+        ppl.ppl_resample_known_max(N, INFER_SEED, lw, max_lw, instance, 0, ancestors=anc, ws=ws)
         if ev:
             ev[3].record(stream)
         ppl.ppl_gather(parts, anc, state_out=parts_out)
@@ -471,7 +472,7 @@ def run_ours(args):
         yd.copy_(yh, non_blocking=True)
         ppl.ppl_infer_is_instance(model, xd, yd, N, INFER_SEED, instance, out=res, lw_out=lw,
                                   particles_out=parts, ws=ws)
-        ppl.ppl_resample(N, INFER_SEED, instance, 0, lw=lw, ancestors=anc, ws=ws)
+        ppl.ppl_resample_known_max(N, INFER_SEED, lw, max_lw, instance, 0, ancestors=anc, ws=ws)
         ppl.ppl_gather(parts, anc, state_out=parts_out)
         res_h.copy_(res, non_blocking=True)
         torch.cuda.synchronize()

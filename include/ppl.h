@@ -154,10 +154,19 @@ ppl_status ppl_logsumexp(const float* lw, int64_t n, double* out_dev, void* ws, 
  * fixed FP32 exponential; q_fixed must sum to at most 2^61.  With T = sum q,
  * step = floor(T / m) and u = floor(w * step / 2^32) (w: word 0 of counter
  * (0, instance, t, RESAMPLE)), ancestors[k] [dev, m] = min{j : q_0 + .. + q_j >
- * u + k * step}.  The prefix sums are exact, so ancestors are bit-exact. */
+ * u + k * step}.  The prefix sums are exact, so ancestors are bit-exact.  The
+ * workspace must be sized for max(n, m) particles. */
 ppl_status ppl_resample(const float* lw, const uint64_t* q_fixed, int64_t n, int64_t m,
                         uint64_t seed, uint32_t instance, uint32_t t, int32_t* ancestors,
                         void* ws, size_t ws_bytes, ppl_stream stream);
+
+/* ppl_resample from lw when the maximum log-weight is already known on the
+ * device, e.g. &out_dev->max_lw of the ppl_infer_is that produced lw (whose
+ * status was PPL_OK): saves a pass over lw.  NaN log-weights are not detected. */
+ppl_status ppl_resample_known_max(const float* lw, const double* max_lw_dev, int64_t n,
+                                  int64_t m, uint64_t seed, uint32_t instance, uint32_t t,
+                                  int32_t* ancestors, void* ws, size_t ws_bytes,
+                                  ppl_stream stream);
 
 /* Gather of the resampled particle state: state_out[k] = state_in[ancestors[k]]
  * for k < m, records of stride_bytes bytes [dev]; state_in holds n_in records.
@@ -282,8 +291,8 @@ ppl_status ppl_infer_is_learned(const ppl_model* model, const float* x, const fl
  * through its own pool, or a real-time loop that must not risk the implicit
  * device synchronisation of cudaMalloc.  The paper has no counterpart; this is
  * a library convenience.  Same arguments and result as ppl_resample, but the
- * scratch is a static device array of about 9.3 MB per device, so n must be at
- * most 2^20 (1048576) particles; larger n returns PPL_EINVAL.  Nothing is
+ * scratch is a static device array of about 9.4 MB per device, so n and m must
+ * be at most 2^20 (1048576); larger sizes return PPL_EINVAL.  Nothing is
  * allocated.  The first call on a device looks the array's address up and
  * caches it (make that first call before any stream capture).  All calls on a
  * device share the array: calls whose work overlaps on the GPU race, so issue

@@ -91,6 +91,10 @@ _SIGS = {
                                     ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
                                     ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_size_t, ctypes.c_void_p]),
+    "ppl_resample_known_max": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                              ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
+                                              ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
+                                              ctypes.c_size_t, ctypes.c_void_p]),
     "ppl_gather": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                   ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                   ctypes.c_void_p]),
@@ -299,7 +303,7 @@ def ppl_resample(m, seed, instance=0, t=0, lw=None, q_fixed=None, ancestors=None
     elif not (q_fixed.is_cuda and q_fixed.dtype in (torch.int64, torch.uint64)):
         raise ValueError("q_fixed must be a 64-bit integer CUDA tensor")
     if ws is None:
-        ws = workspace(poly_model(), n, 0, src.device)
+        ws = workspace(poly_model(), max(n, m), 0, src.device)
     if ancestors is None:
         ancestors = torch.empty(m, dtype=torch.int32, device=src.device)
     st = lib().ppl_resample(_ptr(lw), _ptr(q_fixed), n, int(m), ctypes.c_uint64(seed),
@@ -307,6 +311,27 @@ def ppl_resample(m, seed, instance=0, t=0, lw=None, q_fixed=None, ancestors=None
                             _stream(stream))
     _check(st, "ppl_resample")
     return ancestors
+
+
+def ppl_resample_known_max(m, seed, lw, max_lw_dev, instance=0, t=0, ancestors=None, ws=None,
+                           stream=None):
+    """ppl_resample from lw with its maximum already on the device (float64 scalar)."""
+    _dev_f32(lw, "lw")
+    n = lw.numel()
+    if ws is None:
+        ws = workspace(poly_model(), max(n, m), 0, lw.device)
+    if ancestors is None:
+        ancestors = torch.empty(m, dtype=torch.int32, device=lw.device)
+    st = lib().ppl_resample_known_max(_ptr(lw), ctypes.c_void_p(max_lw_dev.data_ptr()), n,
+                                      int(m), ctypes.c_uint64(seed), int(instance), int(t),
+                                      _ptr(ancestors), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "ppl_resample_known_max")
+    return ancestors
+
+
+def result_max_lw(res_dev):
+    """The device float64 max_lw field of a ppl_is_result buffer (no copy)."""
+    return res_dev[24:32].view(torch.float64)
 
 
 def ppl_gather(state_in, ancestors, state_out=None, stream=None):

@@ -28,6 +28,8 @@ WsLayout layout(int64_t n, int64_t data_len) {
   off += align_up(partials_bytes());
   w.prefix = off;
   off += align_up((size_t)n * sizeof(uint64_t));
+  w.bounds = off;
+  off += align_up((size_t)ancestor_bounds_count(n) * sizeof(int64_t));
   w.lw = off;
   off += align_up((size_t)n * sizeof(float));
   w.scratch = off;
@@ -44,6 +46,7 @@ struct Ws {
   uint64_t* tiles() const { return reinterpret_cast<uint64_t*>(base + l.tiles); }
   void* partials() const { return base + l.partials; }
   uint64_t* prefix() const { return reinterpret_cast<uint64_t*>(base + l.prefix); }
+  int64_t* bounds() const { return reinterpret_cast<int64_t*>(base + l.bounds); }
   float* lw() const { return reinterpret_cast<float*>(base + l.lw); }
   char* scratch() const { return base + l.scratch; }
 };
@@ -191,21 +194,39 @@ ppl_status ppl_logsumexp(const float* lw, int64_t n, double* out_dev, void* ws, 
   return PPL_OK;
 }
 
-ppl_status ppl_resample(const float* lw, const uint64_t* q_fixed, int64_t n, int64_t m,
-                        uint64_t seed, uint32_t instance, uint32_t t, int32_t* ancestors,
-                        void* ws, size_t ws_bytes, ppl_stream stream) {
+static ppl_status resample_impl(const float* lw, const uint64_t* q_fixed, const double* known_max,
+                                int64_t n, int64_t m, uint64_t seed, uint32_t instance,
+                                uint32_t t, int32_t* ancestors, void* ws, size_t ws_bytes,
+                                ppl_stream stream) {
   if ((lw == nullptr) == (q_fixed == nullptr)) return PPL_EINVAL;
   if (!ancestors || n < 1 || n > kMaxParticles || m < 1 || m > kMaxParticles) return PPL_EINVAL;
   Ws w;
-  PPL_TRY(check_ws(ws, ws_bytes, n, 0, &w));
+  PPL_TRY(check_ws(ws, ws_bytes, std::max(n, m), 0, &w));
   cudaStream_t s = (cudaStream_t)stream;
   PPL_TRY(reset_ws(w, true, s));
-  if (lw)
+  if (lw && !known_max)
     PPL_TRY(cuda_status(launch_stats(lw, n, w.hdr(), w.partials(), nullptr, s)));
   PPL_TRY(cuda_status(launch_resample_scan(lw, q_fixed, n, m, seed, instance, t, w.hdr(),
-                                           w.tiles(), w.prefix(), nullptr, s)));
-  PPL_TRY(cuda_status(launch_ancestors(w.prefix(), n, m, w.hdr(), ancestors, nullptr, s)));
+                                           w.tiles(), w.prefix(), nullptr, s, known_max)));
+  PPL_TRY(cuda_status(
+      launch_ancestors(w.prefix(), n, m, w.hdr(), w.bounds(), ancestors, nullptr, s)));
   return PPL_OK;
+}
+
+ppl_status ppl_resample(const float* lw, const uint64_t* q_fixed, int64_t n, int64_t m,
+                        uint64_t seed, uint32_t instance, uint32_t t, int32_t* ancestors,
+                        void* ws, size_t ws_bytes, ppl_stream stream) {
+  return resample_impl(lw, q_fixed, nullptr, n, m, seed, instance, t, ancestors, ws, ws_bytes,
+                       stream);
+}
+
+ppl_status ppl_resample_known_max(const float* lw, const double* max_lw_dev, int64_t n,
+                                  int64_t m, uint64_t seed, uint32_t instance, uint32_t t,
+                                  int32_t* ancestors, void* ws, size_t ws_bytes,
+                                  ppl_stream stream) {
+  if (!lw || !max_lw_dev) return PPL_EINVAL;
+  return resample_impl(lw, nullptr, max_lw_dev, n, m, seed, instance, t, ancestors, ws, ws_bytes,
+                       stream);
 }
 
 ppl_status ppl_gather(const void* state_in, int64_t n_in, int64_t stride_bytes,
@@ -242,7 +263,7 @@ ppl_status ppl_smc_step(const ppl_model* model, float y_t, int32_t t, uint64_t s
                                            logz_est, w.hdr(), w.partials(), s)));
   PPL_TRY(cuda_status(launch_resample_scan(lw, nullptr, n, n, seed, 0, (uint32_t)t, w.hdr(),
                                            w.tiles(), w.prefix(), gate, s)));
-  PPL_TRY(cuda_status(launch_ancestors(w.prefix(), n, n, w.hdr(), anc, gate, s)));
+  PPL_TRY(cuda_status(launch_ancestors(w.prefix(), n, n, w.hdr(), w.bounds(), anc, gate, s)));
   PPL_TRY(cuda_status(launch_gather(x, n, sizeof(float), anc, n, x_tmp, gate, s)));
   PPL_TRY(cuda_status(launch_smc_commit(x, x_tmp, lw, n, gate, s)));
   return PPL_OK;

@@ -47,6 +47,7 @@ struct WsLayout {
   size_t partials;    // per-block partial results
   size_t tiles;       // scan tile status words
   size_t prefix;      // inclusive prefix sums C_j (u64)
+  size_t bounds;      // first ancestor of every output chunk's first and last output
   size_t lw;          // FP32 log-weights when the caller keeps none
   size_t scratch;     // SMC: ancestors + gathered state; host API: data copies
   size_t total;

@@ -33,12 +33,16 @@ constexpr int kScanItems = 8;
 constexpr int64_t kScanTile = (int64_t)kTpb * kScanItems;
 inline int64_t scan_tiles(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
 // gate: when non-null, the kernels do nothing unless *gate != 0 (SMC steps).
+// known_max (optional, device): the maximum log-weight, when a previous pass
+// already found it (the statistics pass is then skipped by the caller).
 cudaError_t launch_resample_scan(const float* lw, const uint64_t* q_fixed, int64_t N, int64_t M,
                                  uint64_t seed, uint32_t instance, uint32_t t, WsHeader* hdr,
                                  uint64_t* tile_status, uint64_t* prefix, const int32_t* gate,
-                                 cudaStream_t s);
+                                 cudaStream_t s, const double* known_max = nullptr);
+int64_t ancestor_bounds_count(int64_t M);
 cudaError_t launch_ancestors(const uint64_t* prefix, int64_t N, int64_t M, const WsHeader* hdr,
-                             int32_t* ancestors, const int32_t* gate, cudaStream_t s);
+                             int64_t* bounds, int32_t* ancestors, const int32_t* gate,
+                             cudaStream_t s);
 cudaError_t launch_gather(const void* in, int64_t n_in, int64_t stride_bytes, const int32_t* anc,
                           int64_t M, void* out, const int32_t* gate, cudaStream_t s);
 

@@ -28,9 +28,11 @@ constexpr size_t kNoAllocHeader = 512;
 constexpr size_t kNoAllocTiles = ((kNoAllocMaxParticles + kScanTile - 1) / kScanTile) * 8;
 constexpr size_t kNoAllocPartials = 4096 * 256;  // >= partials_bytes(), checked at set-up
 constexpr size_t kNoAllocPrefix = kNoAllocMaxParticles * 8;
-constexpr size_t kNoAllocBytes = kNoAllocHeader + kNoAllocTiles + kNoAllocPartials + kNoAllocPrefix;
+constexpr size_t kNoAllocBounds = 2 * ((kNoAllocMaxParticles + 2047) / 2048) * 8;  // >= bounds count
+constexpr size_t kNoAllocBytes =
+    kNoAllocHeader + kNoAllocTiles + kNoAllocPartials + kNoAllocPrefix + kNoAllocBounds;
 
-// About 9.3 MB per device, held from module load until the process exits.
+// About 9.4 MB per device, held from module load until the process exits.
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kMaxDevices = 64;
@@ -60,8 +62,9 @@ extern "C" ppl_status ppl_resample_noalloc(const float* lw, const uint64_t* q_fi
                                            int64_t m, uint64_t seed, uint32_t instance,
                                            uint32_t t, int32_t* ancestors, ppl_stream stream) {
   if ((lw == nullptr) == (q_fixed == nullptr)) return PPL_EINVAL;
-  if (!ancestors || n < 1 || m < 1 || m > 0x7fffffffll) return PPL_EINVAL;
-  if (n > kNoAllocMaxParticles) return PPL_EINVAL;  // beyond the static scratch
+  if (!ancestors || n < 1 || m < 1) return PPL_EINVAL;
+  if (n > kNoAllocMaxParticles || m > kNoAllocMaxParticles) return PPL_EINVAL;  // beyond the static scratch
+  if ((size_t)ancestor_bounds_count(m) * 8 > kNoAllocBounds) return PPL_EINVAL;
   char* base = nullptr;
   const ppl_status st = scratch_for_current_device(&base);
   if (st != PPL_OK) return st;
@@ -79,7 +82,10 @@ extern "C" ppl_status ppl_resample_noalloc(const float* lw, const uint64_t* q_fi
   if (launch_resample_scan(lw, q_fixed, n, m, seed, instance, t, hdr, tiles, prefix, nullptr,
                            s) != cudaSuccess)
     return PPL_ECUDA;
-  if (launch_ancestors(prefix, n, m, hdr, ancestors, nullptr, s) != cudaSuccess) return PPL_ECUDA;
+  int64_t* bounds = reinterpret_cast<int64_t*>(base + kNoAllocHeader + kNoAllocTiles +
+                                               kNoAllocPartials + kNoAllocPrefix);
+  if (launch_ancestors(prefix, n, m, hdr, bounds, ancestors, nullptr, s) != cudaSuccess)
+    return PPL_ECUDA;
   return PPL_OK;
 }
 

@@ -63,7 +63,8 @@ template <bool FROM_LW, bool VEC>
 __global__ void __launch_bounds__(kTpb) resample_scan_kernel(
     const float* __restrict__ lw, const uint64_t* __restrict__ qf, int64_t N, int64_t M,
     uint64_t seed, uint32_t instance, uint32_t t, WsHeader* hdr, uint64_t* tile_status,
-    uint64_t* __restrict__ prefix, const int32_t* gate, int64_t n_tiles) {
+    uint64_t* __restrict__ prefix, const int32_t* gate, int64_t n_tiles,
+    const double* known_max) {
   if (gate && *gate == 0) return;
   __shared__ int64_t tile_sh;
   __shared__ uint64_t warp_tot[kTpb / 32];
@@ -77,7 +78,7 @@ __global__ void __launch_bounds__(kTpb) resample_scan_kernel(
   uint64_t q[kScanItems];
   int bad = 0;
   if (FROM_LW) {
-    const float m = hdr->max_lw;
+    const float m = known_max ? (float)*known_max : hdr->max_lw;
     int S = 0;
     while (((int64_t)1 << S) < N) ++S;
     const float scale = __int_as_float((127 + 61 - S) << 23);
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(kTpb) resample_scan_kernel(
             timed_out = true;
             break;
           }
-          __nanosleep(64);
+          if (spins > 64) __nanosleep(32);
           if ((v >> 62) == 0) v = ld_acquire_u64(tile_status + idx);
         }
         if (timed_out) {
@@ -164,9 +165,18 @@ __global__ void __launch_bounds__(kTpb) resample_scan_kernel(
   __syncthreads();
   const uint64_t tile_excl = excl_sh;
   const uint64_t off = sat_add(tile_excl, thread_excl);
+  if (base + kScanItems <= N) {
+    uint4* dst = reinterpret_cast<uint4*>(prefix + base);
 #pragma unroll
-  for (int j = 0; j < kScanItems; ++j)
-    if (base + j < N) prefix[base + j] = sat_add(off, q[j]);
+    for (int j = 0; j < kScanItems; j += 2) {
+      const uint64_t a = sat_add(off, q[j]), b = sat_add(off, q[j + 1]);
+      dst[j / 2] = make_uint4((uint32_t)a, (uint32_t)(a >> 32), (uint32_t)b, (uint32_t)(b >> 32));
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < kScanItems; ++j)
+      if (base + j < N) prefix[base + j] = sat_add(off, q[j]);
+  }
 
   if (bad) record_status(&hdr->status, PPL_EINVAL);
   if (tile == n_tiles - 1 && tid == 0) {
@@ -188,6 +198,51 @@ __global__ void __launch_bounds__(kTpb) resample_scan_kernel(
   }
 }
 
+constexpr int kAncItems = 8;
+constexpr int64_t kAncChunk = (int64_t)kTpb * kAncItems;
+constexpr int kAncSmem = 4096;
+
+// First index j in [lo, hi) with C[j] > p (hi if none), by one warp: each
+// round the 32 lanes probe 32 evenly spaced positions, so 2^24 entries take
+// five dependent loads.
+__device__ __forceinline__ int64_t warp_upper_bound(const uint64_t* C, int64_t lo, int64_t hi,
+                                                    uint64_t p, int lane) {
+  while (hi - lo > 32) {
+    const int64_t step = (hi - lo + 31) / 32;
+    const int64_t q = lo + (int64_t)(lane + 1) * step - 1;
+    const bool gt = (q >= hi) || (C[q] > p);
+    const unsigned m = __ballot_sync(0xffffffffu, gt);
+    const int f = __ffs(m) - 1;  // m != 0: lane 31 probes at or past hi - 1
+    const int64_t new_lo = (f == 0) ? lo : lo + (int64_t)f * step;
+    hi = (lo + (int64_t)(f + 1) * step - 1) + 1 < hi ? lo + (int64_t)(f + 1) * step : hi;
+    lo = new_lo;
+  }
+  const int64_t q = lo + lane;
+  const bool gt = (q >= hi) || (C[q] > p);
+  const unsigned m = __ballot_sync(0xffffffffu, gt);
+  return m ? lo + (__ffs(m) - 1) : hi;
+}
+
+// bounds[2c], bounds[2c + 1]: the first ancestor of the first and of the last
+// output of chunk c (one warp per bound).
+__global__ void __launch_bounds__(kTpb) chunk_bounds_kernel(const uint64_t* __restrict__ C,
+                                                            int64_t N, int64_t M,
+                                                            const WsHeader* hdr,
+                                                            int64_t* __restrict__ bounds,
+                                                            const int32_t* gate) {
+  if (gate && *gate == 0) return;
+  if (ld_volatile_i32(&hdr->status) != 0) return;
+  const int64_t w = ((int64_t)blockIdx.x * kTpb + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t n_chunks = (M + kAncChunk - 1) / kAncChunk;
+  if (w >= 2 * n_chunks) return;
+  const int64_t c = w >> 1;
+  const int64_t k = (w & 1) ? ((M < (c + 1) * kAncChunk ? M : (c + 1) * kAncChunk) - 1)
+                            : c * kAncChunk;
+  const int64_t j = warp_upper_bound(C, 0, N, hdr->offset + (uint64_t)k * hdr->stride, lane);
+  if (lane == 0) bounds[w] = j < N - 1 ? j : N - 1;
+}
+
 // First index j in [lo, hi) with C[j] > p (hi if none).
 __device__ __forceinline__ int64_t upper_bound_global(const uint64_t* C, int64_t lo, int64_t hi,
                                                       uint64_t p) {
@@ -199,34 +254,28 @@ __device__ __forceinline__ int64_t upper_bound_global(const uint64_t* C, int64_t
   return lo;
 }
 
-constexpr int kAncItems = 8;
-constexpr int64_t kAncChunk = (int64_t)kTpb * kAncItems;
-constexpr int kAncSmem = 4096;
-
 // Output-parallel search: a block owns kAncChunk consecutive outputs, so the
-// work is balanced whatever the weights; the prefix sums it needs are staged
-// in shared memory when they fit.
+// work is balanced whatever the weights; the prefix sums it needs (between the
+// chunk's precomputed bounds) are staged in shared memory when they fit.
 __global__ void __launch_bounds__(kTpb) ancestors_kernel(const uint64_t* __restrict__ C,
                                                          int64_t N, int64_t M,
                                                          const WsHeader* hdr,
+                                                         const int64_t* __restrict__ bounds,
                                                          int32_t* __restrict__ anc,
                                                          const int32_t* gate) {
   if (gate && *gate == 0) return;
   if (ld_volatile_i32(&hdr->status) != 0) return;
   __shared__ uint64_t sC[kAncSmem];
-  __shared__ int64_t jlo_sh, jhi_sh;
   const uint64_t stride = hdr->stride, off = hdr->offset;
   const int tid = threadIdx.x;
   const int64_t n_chunks = (M + kAncChunk - 1) / kAncChunk;
   for (int64_t ch = blockIdx.x; ch < n_chunks; ch += gridDim.x) {
     const int64_t k0 = ch * kAncChunk;
     const int64_t k1 = (M < k0 + kAncChunk ? M : k0 + kAncChunk) - 1;
-    if (tid == 0) jlo_sh = upper_bound_global(C, 0, N, off + (uint64_t)k0 * stride);
-    if (tid == 32) jhi_sh = upper_bound_global(C, 0, N, off + (uint64_t)k1 * stride);
-    __syncthreads();
-    const int64_t jlo = jlo_sh, jhi = (jhi_sh < N - 1 ? jhi_sh : N - 1);
+    const int64_t jlo = bounds[2 * ch], jhi = bounds[2 * ch + 1];
     const int64_t span = jhi - jlo + 1;
     const bool staged = span <= kAncSmem;
+    __syncthreads();
     if (staged)
       for (int64_t j = tid; j < span; j += kTpb) sC[j] = C[jlo + j];
     __syncthreads();
@@ -313,28 +362,34 @@ __global__ void __launch_bounds__(kTpb) gather_kernel(const V* __restrict__ in, 
 cudaError_t launch_resample_scan(const float* lw, const uint64_t* q_fixed, int64_t N, int64_t M,
                                  uint64_t seed, uint32_t instance, uint32_t t, WsHeader* hdr,
                                  uint64_t* tile_status, uint64_t* prefix, const int32_t* gate,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, const double* known_max) {
   const int64_t tiles = scan_tiles(N);
   if (lw) {
     const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15) == 0;
     if (vec)
       resample_scan_kernel<true, true><<<(unsigned)tiles, kTpb, 0, s>>>(
-          lw, nullptr, N, M, seed, instance, t, hdr, tile_status, prefix, gate, tiles);
+          lw, nullptr, N, M, seed, instance, t, hdr, tile_status, prefix, gate, tiles, known_max);
     else
       resample_scan_kernel<true, false><<<(unsigned)tiles, kTpb, 0, s>>>(
-          lw, nullptr, N, M, seed, instance, t, hdr, tile_status, prefix, gate, tiles);
+          lw, nullptr, N, M, seed, instance, t, hdr, tile_status, prefix, gate, tiles, known_max);
   } else {
     resample_scan_kernel<false, false><<<(unsigned)tiles, kTpb, 0, s>>>(
-        nullptr, q_fixed, N, M, seed, instance, t, hdr, tile_status, prefix, gate, tiles);
+        nullptr, q_fixed, N, M, seed, instance, t, hdr, tile_status, prefix, gate, tiles, nullptr);
   }
   return cudaGetLastError();
 }
 
+int64_t ancestor_bounds_count(int64_t M) { return 2 * ((M + kAncChunk - 1) / kAncChunk); }
+
 cudaError_t launch_ancestors(const uint64_t* prefix, int64_t N, int64_t M, const WsHeader* hdr,
-                             int32_t* ancestors, const int32_t* gate, cudaStream_t s) {
+                             int64_t* bounds, int32_t* ancestors, const int32_t* gate,
+                             cudaStream_t s) {
   const int64_t chunks = (M + kAncChunk - 1) / kAncChunk;
+  const int64_t warps = 2 * chunks;
+  chunk_bounds_kernel<<<(unsigned)((warps * 32 + kTpb - 1) / kTpb), kTpb, 0, s>>>(
+      prefix, N, M, hdr, bounds, gate);
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)num_sms() * 8));
-  ancestors_kernel<<<grid, kTpb, 0, s>>>(prefix, N, M, hdr, ancestors, gate);
+  ancestors_kernel<<<grid, kTpb, 0, s>>>(prefix, N, M, hdr, bounds, ancestors, gate);
   return cudaGetLastError();
 }
 

@@ -93,3 +93,17 @@ def test_device_errors_are_reported(ppl):
     ppl.ppl_resample(5000, 0, lw=_t(np.zeros(5000, dtype=np.float32)), ws=ws)
     assert ppl.ppl_workspace_status(ws) == ppl.PPL_OK
     torch.cuda.synchronize()
+
+
+def test_known_max_matches_plain_resample(ppl, orc):
+    import torch
+    x, y = synth.poly_dataset(64, 2)
+    N = 300007
+    model = ppl.poly_model()
+    lw = torch.empty(N, dtype=torch.float32, device="cuda")
+    res = ppl.ppl_infer_is(model, _t(x), _t(y), N, 4, lw_out=lw)
+    a = ppl.ppl_resample_known_max(N, 3, lw, ppl.result_max_lw(res), t=2)
+    b = ppl.ppl_resample(N, 3, t=2, lw=lw)
+    assert torch.equal(a, b)
+    st, ref = orc.resample_from_lw(lw.cpu().numpy(), N, 3, 0, 2)
+    assert st == 0 and np.array_equal(a.cpu().numpy(), ref)
