@@ -179,7 +179,8 @@ def _event_ms(torch, fn, reps):
 
 
 def bench_smc(torch, ppl, reps=5):
-    """Bootstrap filter on the linear-Gaussian model, T = 200, 2^20 particles, one CUDA graph."""
+    """Bootstrap filter on the linear-Gaussian model, T = 200, 2^20 particles: one persistent
+    kernel, with the step-by-step path (one CUDA graph of 200 steps) timed beside it."""
     import numpy as np
 
     import synth
@@ -215,16 +216,29 @@ def bench_smc(torch, ppl, reps=5):
         reset()
         torch.cuda.synchronize()
         times.append(_event_ms(torch, g.replay, 1))
+    ms_steps = float(np.median(times))
+    logz_steps = float(est[-1, 0])
+    # the same filter as one persistent cooperative kernel
+    y_dev = torch.from_numpy(y).cuda()
+    out = ppl.ppl_smc_run(model, y_dev, N, 2, ws=ws)
+    torch.cuda.synchronize()
+    times = [_event_ms(torch, lambda: ppl.ppl_smc_run(model, y_dev, N, 2, ws=ws, out=out), 1)
+             for _ in range(reps)]
+    assert ppl.ppl_workspace_status(ws) == 0
     ms = float(np.median(times))
-    logz = float(est[-1, 0])
+    logz = float(out["log_z"].item())
     import oracle
     kal = oracle.kalman_logz(oracle.lgssm_model(), y)
     return {"workload": "bootstrap filter, linear-Gaussian SSM, T=200, 2^20 particles, FP32 "
-                        "state, resample when ESS < N/2; 200 steps in one CUDA graph",
+                        "state, resample when ESS < N/2; all 200 steps in one persistent "
+                        "cooperative kernel",
             "metric": "particle-steps/sec", "value": N * T / (ms / 1e3), "unit": "particle-steps/s",
-            "ms_per_filter": ms, "resampling_steps": int(flags.sum().item()), "log_z": logz,
-            "kalman_log_z": kal, "abs_err_vs_kalman": abs(logz - kal),
-            "gpu_launches_per_filter": 5 * T}
+            "ms_per_filter": ms, "resampling_steps": int(out["resampled"].sum().item()),
+            "log_z": logz, "kalman_log_z": kal, "abs_err_vs_kalman": abs(logz - kal),
+            "gpu_launches_per_filter": 1,
+            "stepwise_graph": {"ms_per_filter": ms_steps, "log_z": logz_steps,
+                               "gpu_launches_per_filter": 5 * T,
+                               "same_particles": bool(torch.equal(out["x"], x))}}
 
 
 def bench_batched(torch, ppl, reps=5):

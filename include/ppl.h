@@ -168,6 +168,14 @@ ppl_status ppl_resample_known_max(const float* lw, const double* max_lw_dev, int
                                   int32_t* ancestors, void* ws, size_t ws_bytes,
                                   ppl_stream stream);
 
+/* Self-test of failure detection in the resampler's bounded wait: runs the
+ * decoupled-lookback scan over q_fixed [dev, u64, n > 2048] with its first tile
+ * silenced, so every later tile's wait on it expires after max_spin polls
+ * (1..2^22); synchronises and returns the device status, PPL_ETIMEOUT when the
+ * waits ran out as designed.  Nothing hangs: a tile that gives up publishes. */
+ppl_status ppl_selftest_scan_timeout(const uint64_t* q_fixed, int64_t n, int32_t max_spin,
+                                     void* ws, size_t ws_bytes, ppl_stream stream);
+
 /* Gather of the resampled particle state: state_out[k] = state_in[ancestors[k]]
  * for k < m, records of stride_bytes bytes [dev]; state_in holds n_in records.
  * An ancestor outside [0, n_in) yields a zero-filled record instead of a read
@@ -185,6 +193,22 @@ ppl_status ppl_gather(const void* state_in, int64_t n_in, int64_t stride_bytes,
 ppl_status ppl_smc_step(const ppl_model* model, float y_t, int32_t t, uint64_t seed, float* x,
                         float* lw, int64_t n, double* logz_acc, int32_t* resampled,
                         double* logz_est, void* ws, size_t ws_bytes, ppl_stream stream);
+
+/* The whole bootstrap filter of ppl_smc_step for t = 1..T in one persistent
+ * cooperative kernel: x_0 = 0, lw_0 = 0, observations y [dev, FP32, T]; the
+ * particles stay in registers between steps, which are separated by bounded
+ * grid barriers.  Each step computes exactly what ppl_smc_step computes.
+ * Writes x_out, lw_out [dev, n] (the final population), *logz_out [dev, FP64]
+ * (the evidence estimate), resampled_out [dev, int32, T] and ess_out [dev,
+ * FP64, T] (ESS before resampling).  n must fit the resident threads, at
+ * most 8 particles each (about 1.2 million on a GB300: 4 blocks of 256
+ * threads per SM); larger n -> PPL_EINVAL.  A
+ * barrier wait that runs out records PPL_ETIMEOUT in `ws` (read with
+ * ppl_workspace_status) and ends the kernel.  Capturable in a CUDA graph. */
+ppl_status ppl_smc_run(const ppl_model* model, const float* y, int32_t T, uint64_t seed,
+                       int64_t n, float* x_out, float* lw_out, double* logz_out,
+                       int32_t* resampled_out, double* ess_out, void* ws, size_t ws_bytes,
+                       ppl_stream stream);
 
 /* Posterior summary (as ppl_infer_is) of an existing weighted population of
  * line-fitting particles [dev] with log-weights lw [dev]; lw == NULL means

@@ -95,6 +95,9 @@ _SIGS = {
                                               ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
                                               ctypes.c_uint32, ctypes.c_void_p, ctypes.c_void_p,
                                               ctypes.c_size_t, ctypes.c_void_p]),
+    "ppl_selftest_scan_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                                 ctypes.c_void_p, ctypes.c_size_t,
+                                                 ctypes.c_void_p]),
     "ppl_gather": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                   ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                   ctypes.c_void_p]),
@@ -103,6 +106,11 @@ _SIGS = {
                                     ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                     ctypes.c_void_p]),
+    "ppl_smc_run": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                   ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                   ctypes.c_void_p]),
     "ppl_rng_words": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                      ctypes.c_uint32, ctypes.c_int64, ctypes.c_int32,
                                      ctypes.c_void_p, ctypes.c_void_p]),
@@ -329,6 +337,15 @@ def ppl_resample_known_max(m, seed, lw, max_lw_dev, instance=0, t=0, ancestors=N
     return ancestors
 
 
+def ppl_selftest_scan_timeout(q_fixed, max_spin, ws=None, stream=None):
+    """Run the scan with a silent first tile; returns the device status (PPL_ETIMEOUT)."""
+    n = q_fixed.numel()
+    if ws is None:
+        ws = workspace(poly_model(), n, 0, q_fixed.device)
+    return int(lib().ppl_selftest_scan_timeout(_ptr(q_fixed), n, int(max_spin), _ptr(ws),
+                                               ws.numel(), _stream(stream)))
+
+
 def result_max_lw(res_dev):
     """The device float64 max_lw field of a ppl_is_result buffer (no copy)."""
     return res_dev[24:32].view(torch.float64)
@@ -356,6 +373,27 @@ def ppl_smc_step(model, y_t, t, seed, x, lw, logz_acc, resampled, logz_est, ws, 
                             _ptr(x), _ptr(lw), x.numel(), _ptr(logz_acc), _ptr(resampled),
                             _ptr(logz_est), _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "ppl_smc_step")
+
+
+def ppl_smc_run(model, y, n, seed, ws=None, out=None, stream=None):
+    """All T steps of the filter in one kernel; returns a dict of device tensors."""
+    T = y.numel()
+    dev = y.device
+    if ws is None:
+        ws = workspace(model, n, 0, dev)
+    if out is None:
+        out = {"x": torch.empty(n, dtype=torch.float32, device=dev),
+               "lw": torch.empty(n, dtype=torch.float32, device=dev),
+               "log_z": torch.empty(1, dtype=torch.float64, device=dev),
+               "resampled": torch.empty(T, dtype=torch.int32, device=dev),
+               "ess": torch.empty(T, dtype=torch.float64, device=dev)}
+    st = lib().ppl_smc_run(ctypes.byref(model), _ptr(y), T, ctypes.c_uint64(seed), int(n),
+                           _ptr(out["x"]), _ptr(out["lw"]), _ptr(out["log_z"]),
+                           _ptr(out["resampled"]), _ptr(out["ess"]), _ptr(ws), ws.numel(),
+                           _stream(stream))
+    _check(st, "ppl_smc_run")
+    out["ws"] = ws
+    return out
 
 
 def ppl_rng_words(seed, instance, step, purpose, n_particles, n_blocks, out=None, stream=None):

@@ -114,7 +114,9 @@ const char* ppl_status_string(int32_t status) {
 
 size_t ppl_workspace_size(const ppl_model* model, int64_t n_particles, int64_t data_len) {
   if (!model || n_particles < 1 || n_particles > kMaxParticles || data_len < 0) return 0;
-  return layout(n_particles, data_len).total;
+  const size_t total = layout(n_particles, data_len).total;
+  if (model->id == PPL_MODEL_LGSSM) return std::max(total, smc_run_workspace(n_particles));
+  return total;
 }
 
 ppl_status ppl_workspace_status(const void* ws, ppl_stream stream) {
@@ -220,6 +222,19 @@ ppl_status ppl_resample(const float* lw, const uint64_t* q_fixed, int64_t n, int
                        stream);
 }
 
+ppl_status ppl_selftest_scan_timeout(const uint64_t* q_fixed, int64_t n, int32_t max_spin,
+                                     void* ws, size_t ws_bytes, ppl_stream stream) {
+  if (!q_fixed || n <= kScanTile || n > kMaxParticles || max_spin < 1 || max_spin > (1 << 22))
+    return PPL_EINVAL;
+  Ws w;
+  PPL_TRY(check_ws(ws, ws_bytes, n, 0, &w));
+  cudaStream_t s = (cudaStream_t)stream;
+  PPL_TRY(reset_ws(w, true, s));
+  PPL_TRY(cuda_status(launch_scan_timeout_selftest(q_fixed, n, w.hdr(), w.tiles(), w.prefix(),
+                                                   max_spin, s)));
+  return ppl_workspace_status(ws, stream);
+}
+
 ppl_status ppl_resample_known_max(const float* lw, const double* max_lw_dev, int64_t n,
                                   int64_t m, uint64_t seed, uint32_t instance, uint32_t t,
                                   int32_t* ancestors, void* ws, size_t ws_bytes,
@@ -278,6 +293,31 @@ ppl_status ppl_rng_words(uint64_t seed, uint32_t instance, uint32_t step, uint32
   if (reinterpret_cast<uintptr_t>(out_dev) & 15) return PPL_EINVAL;
   return cuda_status(launch_rng_words(seed, instance, step, purpose, n_particles, n_blocks,
                                       out_dev, (cudaStream_t)stream));
+}
+
+ppl_status ppl_smc_run(const ppl_model* model, const float* y, int32_t T, uint64_t seed,
+                       int64_t n, float* x_out, float* lw_out, double* logz_out,
+                       int32_t* resampled_out, double* ess_out, void* ws, size_t ws_bytes,
+                       ppl_stream stream) {
+  if (!model || model->id != PPL_MODEL_LGSSM) return PPL_EINVAL;
+  if (!(model->obs_sigma > 0.0f) || !isfinite(model->phi) || !isfinite(model->q_sigma))
+    return PPL_EINVAL;
+  if (!y || T < 1 || n < 1 || n > kMaxParticles || !x_out || !lw_out || !logz_out ||
+      !resampled_out || !ess_out || !ws || (reinterpret_cast<uintptr_t>(ws) % kAlign))
+    return PPL_EINVAL;
+  if (ws_bytes < smc_run_workspace(n)) return PPL_EINVAL;
+  const double r2 = (double)model->obs_sigma * (double)model->obs_sigma;
+  LgssmParams p;
+  p.phi = model->phi;
+  p.q_sigma = model->q_sigma;
+  p.obs_const = (float)(-0.5 * log(2.0 * M_PI * r2));
+  p.neg_half_inv_r2 = (float)(-1.0 / (2.0 * r2));
+  int32_t* status = nullptr;
+  const cudaError_t e =
+      launch_smc_persistent(p, y, T, seed, n, x_out, lw_out, logz_out, resampled_out, ess_out,
+                            static_cast<char*>(ws), ws_bytes, &status, (cudaStream_t)stream);
+  if (e == cudaErrorInvalidValue) return PPL_EINVAL;
+  return cuda_status(e);
 }
 
 ppl_status ppl_posterior_reduce(const ppl_model* model, const ppl_poly_particle* particles,

@@ -1,0 +1,69 @@
+// Fixed-point resampling weights shared by the resampling kernels: the FP32
+// exponential E32 that decides them and the saturating u64 arithmetic of the
+// prefix sums (see resample.cu for the definition).
+#pragma once
+
+#include "common.cuh"
+
+namespace ppl {
+
+constexpr uint64_t kFlagAgg = 1ull << 62;
+constexpr uint64_t kFlagIncl = 2ull << 62;
+constexpr uint64_t kValMask = (1ull << 62) - 1;
+constexpr uint64_t kLimit = (1ull << 61) + 1;  // saturation: any value above 2^61 is an error
+constexpr int kMaxSpin = 1 << 22;               // bounded wait of the look-back
+
+__device__ __forceinline__ uint64_t sat_add(uint64_t a, uint64_t b) {
+  const uint64_t s = a + b;  // a, b <= kLimit, so no wrap-around
+  return s > kLimit ? kLimit : s;
+}
+
+__device__ __forceinline__ float exp32(float d) {
+  const float kLog2e = 0x1.715476p+0f;   // log2(e), FP32
+  const float kLn2Hi = 0x1.62e4p-1f;     // ln 2 to 16 significant bits
+  const float kLn2Lo = 0x1.7f7d1cp-20f;  // ln 2 - kLn2Hi, FP32
+  const float k = rintf(__fmul_rn(d, kLog2e));
+  float r = __fmaf_rn(-k, kLn2Hi, d);
+  r = __fmaf_rn(-k, kLn2Lo, r);
+  float p = 0x1.a01a02p-13f;             // 1/7!
+  p = __fmaf_rn(p, r, 0x1.6c16c2p-10f);  // 1/6!
+  p = __fmaf_rn(p, r, 0x1.111112p-7f);   // 1/5!
+  p = __fmaf_rn(p, r, 0x1.555556p-5f);   // 1/4!
+  p = __fmaf_rn(p, r, 0x1.555556p-3f);   // 1/3!
+  p = __fmaf_rn(p, r, 0.5f);
+  p = __fmaf_rn(p, r, 1.0f);
+  p = __fmaf_rn(p, r, 1.0f);
+  return __fmul_rn(p, __int_as_float((127 + (int)k) << 23));  // exact: 2^k is normal for k >= -64
+}
+
+__device__ __forceinline__ uint64_t quantize(float lw, float m, float scale) {
+  const float d = __fsub_rn(lw, m);
+  if (!(d >= -44.5f)) return 0;
+  return __float2ull_rz(__fmul_rn(exp32(d), scale));
+}
+
+// First index j in [lo, hi) with C[j] > p (hi if none), by one warp: each
+// round the 32 lanes probe 32 evenly spaced positions, so 2^24 entries take
+// five dependent loads.  L2 = true loads through L2 only, for sums that other
+// blocks of the running kernel wrote.
+template <bool L2 = false>
+__device__ __forceinline__ int64_t warp_upper_bound(const uint64_t* C, int64_t lo, int64_t hi,
+                                                    uint64_t p, int lane) {
+  auto at = [&](int64_t q) { return L2 ? __ldcg(C + q) : C[q]; };
+  while (hi - lo > 32) {
+    const int64_t step = (hi - lo + 31) / 32;
+    const int64_t q = lo + (int64_t)(lane + 1) * step - 1;
+    const bool gt = (q >= hi) || (at(q) > p);
+    const unsigned m = __ballot_sync(0xffffffffu, gt);
+    const int f = __ffs(m) - 1;  // m != 0: lane 31 probes at or past hi - 1
+    const int64_t new_lo = (f == 0) ? lo : lo + (int64_t)f * step;
+    hi = (lo + (int64_t)(f + 1) * step - 1) + 1 < hi ? lo + (int64_t)(f + 1) * step : hi;
+    lo = new_lo;
+  }
+  const int64_t q = lo + lane;
+  const bool gt = (q >= hi) || (at(q) > p);
+  const unsigned m = __ballot_sync(0xffffffffu, gt);
+  return m ? lo + (__ffs(m) - 1) : hi;
+}
+
+}  // namespace ppl

@@ -40,6 +40,9 @@ cudaError_t launch_resample_scan(const float* lw, const uint64_t* q_fixed, int64
                                  uint64_t* tile_status, uint64_t* prefix, const int32_t* gate,
                                  cudaStream_t s, const double* known_max = nullptr);
 int64_t ancestor_bounds_count(int64_t M);
+cudaError_t launch_scan_timeout_selftest(const uint64_t* q, int64_t N, WsHeader* hdr,
+                                         uint64_t* tile_status, uint64_t* prefix, int max_spin,
+                                         cudaStream_t s);
 cudaError_t launch_ancestors(const uint64_t* prefix, int64_t N, int64_t M, const WsHeader* hdr,
                              int64_t* bounds, int32_t* ancestors, const int32_t* gate,
                              cudaStream_t s);
@@ -60,6 +63,11 @@ cudaError_t launch_smc_propagate(const LgssmParams& p, float y_t, int32_t t, uin
                                  float* x, float* lw, int64_t N, double* logz_acc,
                                  int32_t* resampled, double* logz_est, WsHeader* hdr,
                                  void* parts, cudaStream_t s);
+size_t smc_run_workspace(int64_t N);
+cudaError_t launch_smc_persistent(const LgssmParams& p, const float* y, int32_t T, uint64_t seed,
+                                  int64_t N, float* x_out, float* lw_out, double* logz,
+                                  int32_t* resampled, double* ess, char* ws, size_t ws_bytes,
+                                  int32_t** status_out, cudaStream_t s);
 cudaError_t launch_smc_commit(float* x, const float* x_tmp, float* lw, int64_t N,
                               const int32_t* gate, cudaStream_t s);
 

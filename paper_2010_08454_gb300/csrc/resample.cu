@@ -11,45 +11,11 @@
 // E32 is a fixed FP32 exponential (Cody-Waite reduction by ln 2, degree-7
 // Taylor polynomial in Horner form, each step one rounded FP32 operation), so
 // the integers q_i, and hence the ancestors, are reproducible bit for bit.
+#include "fixedpoint.cuh"
 #include "kernels.h"
 #include "rng.cuh"
 
 namespace ppl {
-
-constexpr uint64_t kFlagAgg = 1ull << 62;
-constexpr uint64_t kFlagIncl = 2ull << 62;
-constexpr uint64_t kValMask = (1ull << 62) - 1;
-constexpr uint64_t kLimit = (1ull << 61) + 1;  // saturation: any value above 2^61 is an error
-constexpr int kMaxSpin = 1 << 22;               // bounded wait of the look-back
-
-__device__ __forceinline__ uint64_t sat_add(uint64_t a, uint64_t b) {
-  const uint64_t s = a + b;  // a, b <= kLimit, so no wrap-around
-  return s > kLimit ? kLimit : s;
-}
-
-__device__ __forceinline__ float exp32(float d) {
-  const float kLog2e = 0x1.715476p+0f;   // log2(e), FP32
-  const float kLn2Hi = 0x1.62e4p-1f;     // ln 2 to 16 significant bits
-  const float kLn2Lo = 0x1.7f7d1cp-20f;  // ln 2 - kLn2Hi, FP32
-  const float k = rintf(__fmul_rn(d, kLog2e));
-  float r = __fmaf_rn(-k, kLn2Hi, d);
-  r = __fmaf_rn(-k, kLn2Lo, r);
-  float p = 0x1.a01a02p-13f;             // 1/7!
-  p = __fmaf_rn(p, r, 0x1.6c16c2p-10f);  // 1/6!
-  p = __fmaf_rn(p, r, 0x1.111112p-7f);   // 1/5!
-  p = __fmaf_rn(p, r, 0x1.555556p-5f);   // 1/4!
-  p = __fmaf_rn(p, r, 0x1.555556p-3f);   // 1/3!
-  p = __fmaf_rn(p, r, 0.5f);
-  p = __fmaf_rn(p, r, 1.0f);
-  p = __fmaf_rn(p, r, 1.0f);
-  return __fmul_rn(p, __int_as_float((127 + (int)k) << 23));  // exact: 2^k is normal for k >= -64
-}
-
-__device__ __forceinline__ uint64_t quantize(float lw, float m, float scale) {
-  const float d = __fsub_rn(lw, m);
-  if (!(d >= -44.5f)) return 0;
-  return __float2ull_rz(__fmul_rn(exp32(d), scale));
-}
 
 __device__ __forceinline__ uint64_t warp_sum_sat(uint64_t v) {
 #pragma unroll
@@ -64,7 +30,7 @@ __global__ void __launch_bounds__(kTpb) resample_scan_kernel(
     const float* __restrict__ lw, const uint64_t* __restrict__ qf, int64_t N, int64_t M,
     uint64_t seed, uint32_t instance, uint32_t t, WsHeader* hdr, uint64_t* tile_status,
     uint64_t* __restrict__ prefix, const int32_t* gate, int64_t n_tiles,
-    const double* known_max) {
+    const double* known_max, int64_t silent_tile, int max_spin) {
   if (gate && *gate == 0) return;
   __shared__ int64_t tile_sh;
   __shared__ uint64_t warp_tot[kTpb / 32];
@@ -124,6 +90,8 @@ __global__ void __launch_bounds__(kTpb) resample_scan_kernel(
   }
   const uint64_t thread_excl = sat_add(warp_excl, inc - own);
 
+  // A silent tile publishes nothing (self-test of the bounded wait only).
+  if (tile == silent_tile) return;
   // publish the aggregate, then look back for the exclusive prefix
   if (warp == 0) {
     uint64_t excl = 0;
@@ -138,7 +106,7 @@ __global__ void __launch_bounds__(kTpb) resample_scan_kernel(
         uint64_t v = (idx < 0) ? kFlagIncl : ld_acquire_u64(tile_status + idx);
         int spins = 0;
         while (__any_sync(0xffffffffu, (v >> 62) == 0)) {
-          if (++spins > kMaxSpin) {
+          if (++spins > max_spin) {
             timed_out = true;
             break;
           }
@@ -201,27 +169,6 @@ __global__ void __launch_bounds__(kTpb) resample_scan_kernel(
 constexpr int kAncItems = 8;
 constexpr int64_t kAncChunk = (int64_t)kTpb * kAncItems;
 constexpr int kAncSmem = 4096;
-
-// First index j in [lo, hi) with C[j] > p (hi if none), by one warp: each
-// round the 32 lanes probe 32 evenly spaced positions, so 2^24 entries take
-// five dependent loads.
-__device__ __forceinline__ int64_t warp_upper_bound(const uint64_t* C, int64_t lo, int64_t hi,
-                                                    uint64_t p, int lane) {
-  while (hi - lo > 32) {
-    const int64_t step = (hi - lo + 31) / 32;
-    const int64_t q = lo + (int64_t)(lane + 1) * step - 1;
-    const bool gt = (q >= hi) || (C[q] > p);
-    const unsigned m = __ballot_sync(0xffffffffu, gt);
-    const int f = __ffs(m) - 1;  // m != 0: lane 31 probes at or past hi - 1
-    const int64_t new_lo = (f == 0) ? lo : lo + (int64_t)f * step;
-    hi = (lo + (int64_t)(f + 1) * step - 1) + 1 < hi ? lo + (int64_t)(f + 1) * step : hi;
-    lo = new_lo;
-  }
-  const int64_t q = lo + lane;
-  const bool gt = (q >= hi) || (C[q] > p);
-  const unsigned m = __ballot_sync(0xffffffffu, gt);
-  return m ? lo + (__ffs(m) - 1) : hi;
-}
 
 // bounds[2c], bounds[2c + 1]: the first ancestor of the first and of the last
 // output of chunk c (one warp per bound).
@@ -368,14 +315,29 @@ cudaError_t launch_resample_scan(const float* lw, const uint64_t* q_fixed, int64
     const bool vec = (reinterpret_cast<uintptr_t>(lw) & 15) == 0;
     if (vec)
       resample_scan_kernel<true, true><<<(unsigned)tiles, kTpb, 0, s>>>(
-          lw, nullptr, N, M, seed, instance, t, hdr, tile_status, prefix, gate, tiles, known_max);
+          lw, nullptr, N, M, seed, instance, t, hdr, tile_status, prefix, gate, tiles, known_max, -1,
+          kMaxSpin);
     else
       resample_scan_kernel<true, false><<<(unsigned)tiles, kTpb, 0, s>>>(
-          lw, nullptr, N, M, seed, instance, t, hdr, tile_status, prefix, gate, tiles, known_max);
+          lw, nullptr, N, M, seed, instance, t, hdr, tile_status, prefix, gate, tiles, known_max, -1,
+          kMaxSpin);
   } else {
     resample_scan_kernel<false, false><<<(unsigned)tiles, kTpb, 0, s>>>(
-        nullptr, q_fixed, N, M, seed, instance, t, hdr, tile_status, prefix, gate, tiles, nullptr);
+        nullptr, q_fixed, N, M, seed, instance, t, hdr, tile_status, prefix, gate, tiles, nullptr, -1,
+        kMaxSpin);
   }
+  return cudaGetLastError();
+}
+
+// Self-test of the bounded look-back wait: tile 0 of a fixed-point scan
+// publishes nothing, so every other tile's wait runs out after max_spin polls
+// and records PPL_ETIMEOUT; each still publishes, so no tile waits forever.
+cudaError_t launch_scan_timeout_selftest(const uint64_t* q, int64_t N, WsHeader* hdr,
+                                         uint64_t* tile_status, uint64_t* prefix, int max_spin,
+                                         cudaStream_t s) {
+  const int64_t tiles = scan_tiles(N);
+  resample_scan_kernel<false, false><<<(unsigned)tiles, kTpb, 0, s>>>(
+      nullptr, q, N, N, 0, 0, 0, hdr, tile_status, prefix, nullptr, tiles, nullptr, 0, max_spin);
   return cudaGetLastError();
 }
 

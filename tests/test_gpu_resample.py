@@ -107,3 +107,16 @@ def test_known_max_matches_plain_resample(ppl, orc):
     assert torch.equal(a, b)
     st, ref = orc.resample_from_lw(lw.cpu().numpy(), N, 3, 0, 2)
     assert st == 0 and np.array_equal(a.cpu().numpy(), ref)
+
+
+def test_bounded_wait_reports_timeout_and_recovers(ppl):
+    # a tile that never publishes makes every later tile's bounded wait expire;
+    # the status comes back as PPL_ETIMEOUT and the context stays usable
+    import torch
+    q = _t(synth.fixed_weights(5 * 2048 + 17, 3).view(np.int64))
+    assert ppl.ppl_selftest_scan_timeout(q, 1 << 12) == ppl.PPL_ETIMEOUT
+    anc = ppl.ppl_resample(1000, 1, q_fixed=q)
+    ws = ppl.workspace(ppl.poly_model(), q.numel())
+    ppl.ppl_resample(1000, 1, q_fixed=q, ancestors=anc, ws=ws)
+    assert ppl.ppl_workspace_status(ws) == ppl.PPL_OK
+    torch.cuda.synchronize()

@@ -84,3 +84,20 @@ def test_first_step_state_is_the_reproducible_normal_bit_for_bit(ppl, orc):
     for i in list(range(0, N, 997)) + [N - 1]:
         ref = np.float32(orc.normal32(int(words[i, 0, 0]), int(words[i, 0, 1])))
         assert xs[i] == ref, (i, xs[i], ref)
+
+
+@pytest.mark.parametrize("N,T", [(1, 5), (4099, 40), (1 << 20, 200)])
+def test_persistent_filter_matches_stepwise_and_oracle(ppl, orc, N, T):
+    import torch
+    y = synth.lgssm_dataset(T, 2)
+    out = ppl.ppl_smc_run(ppl.lgssm_model(), torch.from_numpy(y).cuda(), N, 7)
+    assert ppl.ppl_workspace_status(out["ws"]) == 0
+    g = run_smc(ppl, y, N, 7)
+    assert np.array_equal(out["resampled"].cpu().numpy(), g["resampled"])
+    assert np.array_equal(out["x"].cpu().numpy(), g["x"])  # same particles, bit for bit
+    assert np.array_equal(out["lw"].cpu().numpy(), g["lw"])
+    # the two sum the FP32 block partials in different groupings: ~1e-7 per step
+    np.testing.assert_allclose(out["ess"].cpu().numpy(), g["ess"], rtol=1e-5)
+    assert abs(float(out["log_z"].item()) - g["log_z"]) < 1e-6 * T
+    r = orc.smc_lgssm(orc.lgssm_model(), y, N, 7, state_f32=True)
+    assert abs(float(out["log_z"].item()) - r["log_z"]) <= 1e-3
