@@ -192,7 +192,7 @@ def bench_smc(torch, ppl, reps=5):
     acc = torch.zeros(1, dtype=torch.float64, device="cuda")
     flags = torch.zeros(T, dtype=torch.int32, device="cuda")
     est = torch.zeros((T, 2), dtype=torch.float64, device="cuda")
-    ws = ppl.workspace(model, N)
+    ws = ppl.workspace(model, N, T)
 
     def run_steps():
         for t in range(1, T + 1):

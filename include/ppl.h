@@ -201,10 +201,13 @@ ppl_status ppl_smc_step(const ppl_model* model, float y_t, int32_t t, uint64_t s
  * Writes x_out, lw_out [dev, n] (the final population), *logz_out [dev, FP64]
  * (the evidence estimate), resampled_out [dev, int32, T] and ess_out [dev,
  * FP64, T] (ESS before resampling).  n must fit the resident threads, at
- * most 8 particles each (about 1.2 million on a GB300: 4 blocks of 256
- * threads per SM); larger n -> PPL_EINVAL.  A
+ * most 8 particles each (about 1.2 million on a GB300: one block of 1024
+ * threads per SM); larger n, or T > 2^27, -> PPL_EINVAL.  A
  * barrier wait that runs out records PPL_ETIMEOUT in `ws` (read with
- * ppl_workspace_status) and ends the kernel.  Capturable in a CUDA graph. */
+ * ppl_workspace_status) and ends the kernel.  `ws` holds at least
+ * ppl_workspace_size(model, n, T) bytes.  The per-step normalising sums are
+ * kept as FP32 pairs (about 48 significant bits); log Z and the ESS are formed
+ * from them in FP64 after the last step.  Capturable in a CUDA graph. */
 ppl_status ppl_smc_run(const ppl_model* model, const float* y, int32_t T, uint64_t seed,
                        int64_t n, float* x_out, float* lw_out, double* logz_out,
                        int32_t* resampled_out, double* ess_out, void* ws, size_t ws_bytes,

@@ -380,7 +380,7 @@ def ppl_smc_run(model, y, n, seed, ws=None, out=None, stream=None):
     T = y.numel()
     dev = y.device
     if ws is None:
-        ws = workspace(model, n, 0, dev)
+        ws = workspace(model, n, T, dev)
     if out is None:
         out = {"x": torch.empty(n, dtype=torch.float32, device=dev),
                "lw": torch.empty(n, dtype=torch.float32, device=dev),

@@ -115,7 +115,7 @@ const char* ppl_status_string(int32_t status) {
 size_t ppl_workspace_size(const ppl_model* model, int64_t n_particles, int64_t data_len) {
   if (!model || n_particles < 1 || n_particles > kMaxParticles || data_len < 0) return 0;
   const size_t total = layout(n_particles, data_len).total;
-  if (model->id == PPL_MODEL_LGSSM) return std::max(total, smc_run_workspace(n_particles));
+  if (model->id == PPL_MODEL_LGSSM) return std::max(total, smc_run_workspace(n_particles, data_len));
   return total;
 }
 
@@ -305,7 +305,7 @@ ppl_status ppl_smc_run(const ppl_model* model, const float* y, int32_t T, uint64
   if (!y || T < 1 || n < 1 || n > kMaxParticles || !x_out || !lw_out || !logz_out ||
       !resampled_out || !ess_out || !ws || (reinterpret_cast<uintptr_t>(ws) % kAlign))
     return PPL_EINVAL;
-  if (ws_bytes < smc_run_workspace(n)) return PPL_EINVAL;
+  if (ws_bytes < smc_run_workspace(n, T)) return PPL_EINVAL;
   const double r2 = (double)model->obs_sigma * (double)model->obs_sigma;
   LgssmParams p;
   p.phi = model->phi;

@@ -36,24 +36,33 @@ __device__ __forceinline__ float exp32(float d) {
   return __fmul_rn(p, __int_as_float((127 + (int)k) << 23));  // exact: 2^k is normal for k >= -64
 }
 
+// floor(v) for finite 0 <= v < 2^64, from the bits of v (the same value as a
+// truncating conversion; integer operations only, which keeps the 64-bit
+// conversion off this GPU's narrow FP64 pipe).
+__device__ __forceinline__ uint64_t floor_u64(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const int ex = (int)(b >> 23) - 150;  // v = mant * 2^ex for normal v
+  if ((b >> 23) == 0 || ex < -24) return 0;
+  if (ex > 40) return ~0ull;  // v >= 2^64 (never for the weights here)
+  const uint64_t mant = (uint64_t)((b & 0x7fffffu) | 0x800000u);
+  return ex >= 0 ? mant << ex : mant >> -ex;
+}
+
 __device__ __forceinline__ uint64_t quantize(float lw, float m, float scale) {
   const float d = __fsub_rn(lw, m);
   if (!(d >= -44.5f)) return 0;
-  return __float2ull_rz(__fmul_rn(exp32(d), scale));
+  return floor_u64(__fmul_rn(exp32(d), scale));
 }
 
 // First index j in [lo, hi) with C[j] > p (hi if none), by one warp: each
 // round the 32 lanes probe 32 evenly spaced positions, so 2^24 entries take
-// five dependent loads.  L2 = true loads through L2 only, for sums that other
-// blocks of the running kernel wrote.
-template <bool L2 = false>
+// five dependent loads.
 __device__ __forceinline__ int64_t warp_upper_bound(const uint64_t* C, int64_t lo, int64_t hi,
                                                     uint64_t p, int lane) {
-  auto at = [&](int64_t q) { return L2 ? __ldcg(C + q) : C[q]; };
   while (hi - lo > 32) {
     const int64_t step = (hi - lo + 31) / 32;
     const int64_t q = lo + (int64_t)(lane + 1) * step - 1;
-    const bool gt = (q >= hi) || (at(q) > p);
+    const bool gt = (q >= hi) || (C[q] > p);
     const unsigned m = __ballot_sync(0xffffffffu, gt);
     const int f = __ffs(m) - 1;  // m != 0: lane 31 probes at or past hi - 1
     const int64_t new_lo = (f == 0) ? lo : lo + (int64_t)f * step;
@@ -61,7 +70,7 @@ __device__ __forceinline__ int64_t warp_upper_bound(const uint64_t* C, int64_t l
     lo = new_lo;
   }
   const int64_t q = lo + lane;
-  const bool gt = (q >= hi) || (at(q) > p);
+  const bool gt = (q >= hi) || (C[q] > p);
   const unsigned m = __ballot_sync(0xffffffffu, gt);
   return m ? lo + (__ffs(m) - 1) : hi;
 }

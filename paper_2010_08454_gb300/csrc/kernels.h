@@ -63,7 +63,7 @@ cudaError_t launch_smc_propagate(const LgssmParams& p, float y_t, int32_t t, uin
                                  float* x, float* lw, int64_t N, double* logz_acc,
                                  int32_t* resampled, double* logz_est, WsHeader* hdr,
                                  void* parts, cudaStream_t s);
-size_t smc_run_workspace(int64_t N);
+size_t smc_run_workspace(int64_t N, int64_t T);
 cudaError_t launch_smc_persistent(const LgssmParams& p, const float* y, int32_t T, uint64_t seed,
                                   int64_t N, float* x_out, float* lw_out, double* logz,
                                   int32_t* resampled, double* ess, char* ws, size_t ws_bytes,

@@ -1,71 +1,191 @@
 // The whole bootstrap particle filter on the linear-Gaussian state-space model
 // in one persistent, cooperative kernel (particle methods: the paper's stated
-// future work, §6; observe as in §3.4, Fig. 2).  Each thread keeps its
-// particles' state and log-weights in registers for all T steps; the steps are
-// separated by grid barriers instead of kernel launches.  The arithmetic of a
-// step is exactly that of ppl_smc_step (same draws, same FP32 operations, same
-// fixed-point systematic resampling), so both give the same particles.
+// future work, §6; observe as in §3.4, Fig. 2).  One block of 1024 threads per
+// SM; each thread keeps its R particles' state and log-weights in registers
+// for all T steps; the steps are separated by grid barriers instead of kernel
+// launches.  The arithmetic of a step is exactly that of ppl_smc_step (same
+// draws, same FP32 operations, same fixed-point systematic resampling), so
+// both give the same particles.
 //
-// Barriers spin on a generation counter with a bound; a block whose wait runs
-// out records PPL_ETIMEOUT and every block leaves at its next barrier, so the
-// kernel always ends.  The launch is cooperative, which guarantees that all
-// blocks are resident at once (or fails to launch).
+// A step is: propagate and weight (registers) -> block partial -> barrier 1,
+// whose last arriving block merges the partials and takes the resampling
+// decision for everyone (published in the release word itself); when
+// resampling: fixed-point weights and block totals -> barrier 2, whose last
+// block scans the totals and tells every block which output slots its
+// particles are the ancestors of -> each block finds those ancestors by a
+// merge of its prefix sums with the slots' positions, in shared memory, and
+// writes the slots -> barrier 3 -> every thread reads its slots.
+//
+// Every barrier wait is bounded; a block whose wait runs out records
+// PPL_ETIMEOUT and every block leaves at its next wait, so the kernel always
+// ends.  The launch is cooperative, which guarantees that all blocks are
+// resident at once (or fails to launch).
 #include <algorithm>
 
 #include "fixedpoint.cuh"
 #include "kernels.h"
 #include "rng.cuh"
-#include "stats.cuh"
 
 namespace ppl {
 
+constexpr int kSmcTpb = 1024;          // threads of a block: one block per SM
+constexpr int kSmcWarps = kSmcTpb / 32;
 constexpr int kSmcSpin = 1 << 22;      // bound of one barrier wait (polls)
-constexpr int kSmcSmem = 4096;         // prefix sums staged per block for the ancestor search
+constexpr int kSmcMaxGrid = kSmcTpb;   // the merging block holds one partial per thread
+constexpr int kSmcOut = 24576;         // outputs a block stages in shared memory
 
-// Control words at offset 0 of the workspace: the status first, where
-// ppl_workspace_status reads it.
-struct SmcCtl {
-  int32_t status;
-  unsigned count, gen;  // barrier
-  int32_t pad;
+// A block's normalisation partial: m = max lw, s = sum exp(lw - m),
+// s2 = sum exp(2 (lw - m)), nan = some lw is NaN.  One 16-byte load.
+struct __align__(16) SmcPart {
+  float m, s, s2;
+  int nan;
 };
 
-// Grid barrier with a bounded wait.  Returns false when the kernel must stop.
-__device__ __forceinline__ bool grid_barrier(SmcCtl* ctl, unsigned nblocks) {
-  __shared__ bool ok;
-  __threadfence();
-  __syncthreads();
+// What one step leaves for the evidence and ESS outputs, which are formed in
+// FP64 once after the last step: M the maximum log-weight, S and S2 the sums of
+// exp(lw - M) and exp(2 (lw - M)) as unevaluated FP32 pairs.
+struct __align__(16) SmcStep {
+  float M, s_hi, s_lo, s2_hi, s2_lo;
+  int32_t flag, pad[2];
+};
+
+// Control block at offset 0 of the workspace.  Line 0: the status (first, where
+// ppl_workspace_status reads it) and the arrival counter; line 1: the release
+// word and what the last block of barrier 2 publishes with it.  The release
+// word is (barrier number << 34) | payload; barrier 1's payload is
+// bad << 33 | resample << 32 | bits of M.
+struct __align__(128) SmcCtl {
+  int32_t status;
+  int32_t pad0;
+  unsigned long long arrive;  // arrivals so far: barrier e is complete at e * grid
+  char pad1[112];
+  unsigned long long release;
+  unsigned long long pad2;
+  unsigned long long total, stride, offset;  // T, floor(T / N), u
+};
+
+// Double-float arithmetic (pairs hi + lo, |lo| <= ulp(hi) / 2): Knuth's
+// TwoSum for the sum, an FMA-exact product (Dekker's TwoProduct).  The
+// per-step sums stay off the FP64 pipe, which is narrow on this GPU.
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  const float t = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  const float hi = __fadd_rn(s, t);
+  return make_float2(hi, __fsub_rn(t, __fsub_rn(hi, s)));
+}
+__device__ __forceinline__ float2 df_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return make_float2(p, __fmaf_rn(a, b, -p));
+}
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  float2 p = df_prod(a.x, b.x);
+  p.y = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, p.y));
+  const float hi = __fadd_rn(p.x, p.y);
+  return make_float2(hi, __fsub_rn(p.y, __fsub_rn(hi, p.x)));
+}
+__device__ __forceinline__ float2 df_warp_sum(float2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = df_add(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, o),
+                              __shfl_xor_sync(0xffffffffu, v.y, o)));
+  return v;
+}
+// Inclusive warp scan of saturating 64-bit sums.
+__device__ __forceinline__ uint64_t warp_scan_u64(uint64_t v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v = sat_add(v, u);
+  }
+  return v;
+}
+
+// The leading 24 bits of v > 0 as an FP32 number (relative error below
+// 2^-23), through 32-bit conversions only.
+__device__ __forceinline__ float lead_f32(uint64_t v) {
+  const int sh = max(0, 40 - __clzll(v));  // v >> sh < 2^24
+  return __fmul_rn(__uint2float_rn((uint32_t)(v >> sh)), __int_as_float((127 + sh) << 23));
+}
+
+// ceil(num / den) for 0 < num, den < 2^62 and a quotient below 2^22: an FP32
+// estimate (relative error below 2^-21, so within two of the quotient), then
+// exact integer corrections.
+__device__ __forceinline__ uint64_t ceil_div_small(uint64_t num, uint64_t den) {
+  uint64_t k = __float2uint_rz(__fdividef(lead_f32(num), lead_f32(den)));
+  for (int i = 0; i < 4 && k * den < num; ++i) ++k;
+  for (int i = 0; i < 4 && k > 0 && (k - 1) * den >= num; ++i) --k;
+  if (k * den < num || (k > 0 && (k - 1) * den >= num)) k = (num + den - 1) / den;  // never taken
+  return k;
+}
+
+__device__ __forceinline__ unsigned long long atom_add_acq_rel(unsigned long long* p,
+                                                               unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;"
+               : "=l"(old)
+               : "l"(p), "l"(v)
+               : "memory");
+  return old;
+}
+
+// Grid barrier number e (1-based; every block counts its own).  After a block
+// barrier, thread 0 arrives with an acquire-release atomic.  Without a job the
+// others poll the arrival count.  With one, the block whose arrival completes
+// the count runs `job` with all its threads (thread 0's return value is the
+// payload) and releases the others, which poll the release word; every block
+// finds the release word in *rel.  Thread 0 then runs `after` before the
+// closing block barrier.  Returns false when the kernel must stop.
+template <bool kJob, class Job, class After>
+__device__ __forceinline__ bool grid_sync(SmcCtl* ctl, unsigned G, unsigned long long e,
+                                          unsigned long long* rel, Job&& job, After&& after) {
+  __shared__ int role;  // 1: ran the job, 0: released, -1: stop
+  __syncthreads();      // the block's writes precede thread 0's release
   if (threadIdx.x == 0) {
-    ok = true;
-    if (ld_volatile_i32(&ctl->status) != 0) {
-      ok = false;
+    const unsigned long long target = e * G;
+    const unsigned long long old = atom_add_acq_rel(&ctl->arrive, 1ull);
+    int r = 0;
+    if (old == target - 1) {
+      r = kJob ? 1 : 0;
     } else {
-      const unsigned g = *reinterpret_cast<volatile unsigned*>(&ctl->gen);
-      __threadfence();
-      if (atomicAdd(&ctl->count, 1u) == nblocks - 1) {
-        atomicExch(&ctl->count, 0u);
-        __threadfence();
-        atomicAdd(&ctl->gen, 1u);
-      } else {
-        int spins = 0;
-        while (*reinterpret_cast<volatile unsigned*>(&ctl->gen) == g) {
-          if (ld_volatile_i32(&ctl->status) != 0) {  // another block gave up
-            ok = false;
-            break;
-          }
-          if (++spins > kSmcSpin) {
-            record_status(&ctl->status, PPL_ETIMEOUT);
-            ok = false;
-            break;
-          }
-          if (spins > 32) __nanosleep(64);
+      const uint64_t* word =
+          reinterpret_cast<const uint64_t*>(kJob ? &ctl->release : &ctl->arrive);
+      int spins = 0;
+      for (;;) {
+        const unsigned long long v = ld_acquire_u64(word);
+        if (kJob ? (v >> 34) >= e : v >= target) {
+          if (kJob) *rel = v;
+          break;
         }
+        if ((spins & 15) == 15 && ld_volatile_i32(&ctl->status) != 0) {  // another block gave up
+          r = -1;
+          break;
+        }
+        if (++spins > kSmcSpin) {
+          record_status(&ctl->status, PPL_ETIMEOUT);
+          r = -1;
+          break;
+        }
+        if (spins > 32) __nanosleep(32);
       }
-      __threadfence();
     }
+    role = r;
   }
   __syncthreads();
-  return ok;
+  const int r = role;
+  if (r == 1) {
+    const unsigned long long payload = job();
+    __syncthreads();  // the job's writes precede the release
+    if (threadIdx.x == 0) {
+      const unsigned long long v = (e << 34) | payload;
+      st_release_u64(reinterpret_cast<uint64_t*>(&ctl->release), v);
+      *rel = v;
+    }
+  }
+  if (r >= 0 && threadIdx.x == 0) after();
+  __syncthreads();
+  return r >= 0;
 }
 
 struct SmcArgs {
@@ -80,45 +200,59 @@ struct SmcArgs {
   int32_t* resampled;  // [T]
   double* ess;         // [T]
   SmcCtl* ctl;
-  StatPartial* parts;  // [2 x grid]
-  uint64_t* bsum;      // [grid]
-  uint64_t* C;         // [N]
-  float* xbuf;         // [N]
+  SmcPart* parts;      // [grid]
+  uint64_t* bsum;      // [grid] block totals of the fixed-point weights
+  uint64_t* bexcl;     // [grid] their exclusive prefix
+  int64_t* kstart;     // [grid + 1] first output slot whose ancestor each block holds
+  SmcStep* stash;      // [T]
+  float* xbuf;         // [N] the resampled states, by output slot
 };
 
-// Thread `tid` of block b holds particles i0 .. i0 + R - 1, i0 = (b kTpb + tid) R,
+// Thread `tid` of block b holds particles i0 .. i0 + R - 1, i0 = (b kSmcTpb + tid) R,
 // so a thread's fixed-point weights are consecutive terms of the prefix sum.
 template <int R>
-__global__ void __launch_bounds__(kTpb, 4) smc_persistent_kernel(SmcArgs a) {
-  __shared__ uint64_t sC[kSmcSmem];
-  __shared__ uint64_t warp_tot[kTpb / 32];
-  __shared__ uint64_t red[2][kTpb / 32];
-  __shared__ int64_t bound_sh[2];
-  __shared__ double stat_sh[3];
-  __shared__ float M_sh;
-  __shared__ int nan_sh;
+__global__ void __launch_bounds__(kSmcTpb, 1) smc_persistent_kernel(SmcArgs a) {
+  constexpr int64_t P = (int64_t)kSmcTpb * R;  // particles of one block
+  extern __shared__ __align__(16) unsigned char smc_dyn[];
+  uint64_t* sA = reinterpret_cast<uint64_t*>(smc_dyn);  // [P] weights, then local prefix sums
+  float* sX = reinterpret_cast<float*>(sA + P);           // [P] states
+  float* sx = sX + P;                                     // [kSmcOut] this block's outputs
+  __shared__ float sh_max[kSmcWarps];
+  __shared__ int sh_nan[kSmcWarps];
+  __shared__ float2 sh_s[kSmcWarps];
+  __shared__ float j_max[kSmcWarps];
+  __shared__ int j_nan[kSmcWarps];
+  __shared__ float2 j_s[kSmcWarps], j_s2[kSmcWarps];
+  __shared__ uint64_t sh_tot[kSmcWarps], j_tot[kSmcWarps];
+  __shared__ double sh_z[kSmcWarps];
+  __shared__ unsigned long long rel;
+  __shared__ uint64_t view[6];  // T, stride, u, C at the block start, K_b, K_b+1
+  __shared__ uint64_t j_view[2];
+  __shared__ uint32_t resample_word;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned G = gridDim.x;
-  const int64_t base = (int64_t)blockIdx.x * kTpb * R;
-  const int64_t i0 = base + (int64_t)tid * R;
+  const int64_t i0 = (int64_t)blockIdx.x * P + (int64_t)tid * R;
   const int64_t N = a.N;
+  SmcCtl* ctl = a.ctl;
   float x[R], lw[R];
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     x[r] = 0.0f;
     lw[r] = 0.0f;
   }
-  double logz_acc = 0.0, last_lse = 0.0;
-  bool last_resampled = false;
-  const double log_n = log((double)N);
   int S = 0;
   while (((int64_t)1 << S) < N) ++S;
   const float scale = __int_as_float((127 + 61 - S) << 23);  // 2^(61 - ceil(log2 N))
+  const float half_n = 0.5f * (float)N;                      // exact: N < 2^24
+  unsigned long long e = 0;                                  // barriers passed
+  float y_next = a.y[0];
 
   for (int t = 1; t <= a.T; ++t) {
-    const float yt = a.y[t - 1];
-    StatAcc acc;
-    acc.init();
+    if (tid == 0) resample_word = philox_block(a.seed, 0, 0, (uint32_t)t, kResample, 0).x;
+    const float yt = y_next;
+    if (t < a.T) y_next = __ldg(a.y + t);  // in flight during this step
+    int nan = 0;
+    float tm = -INFINITY;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int64_t i = i0 + r;
@@ -132,187 +266,263 @@ __global__ void __launch_bounds__(kTpb, 4) smc_persistent_kernel(SmcArgs a) {
             lw[r], __fadd_rn(a.p.obs_const, __fmul_rn(__fmul_rn(a.p.neg_half_inv_r2, d), d)));
         x[r] = xi;
         lw[r] = li;
-        acc.add(li, (int)i, -1);
+        nan |= (li != li);
+        tm = fmaxf(tm, li);
       }
     }
-    // partials are double-buffered by step parity: a block can be at most one
-    // barrier ahead, so it never overwrites partials another block still reads
-    StatPartial* parts = a.parts + (size_t)(t & 1) * G;
-    {
-      StatAcc br = block_reduce_stat(acc);
-      if (tid == 0) to_partial(br, parts + blockIdx.x);
+    // block partial: the maximum (every warp reduces the 32 warp maxima), then
+    // the sums around it (warp 0 adds the 32 warp sums)
+    tm = warp_max(tm);
+    nan = __any_sync(0xffffffffu, nan);
+    if (lane == 0) {
+      sh_max[warp] = tm;
+      sh_nan[warp] = nan;
     }
-    if (!grid_barrier(a.ctl, G)) return;
-    // every block merges all partials in the same fixed order, so every block
-    // holds the same LSE and ESS and takes the same resampling decision
-    {
-      StatAcc m;
-      m.init();
-      for (unsigned b = tid; b < G; b += kTpb) {
-        const StatPartial* q = parts + b;
-        StatAcc o;
-        o.init();
-        o.m = __ldcg(&q->m);
-        o.s = __ldcg(&q->s);
-        o.s2 = __ldcg(&q->s2);
-        o.arg = __ldcg(&q->arg);
-        o.nan = __ldcg(&q->nan);
-        m.merge(o);
-      }
-      StatAcc rr = block_reduce_stat(m);
-      if (tid == 0) {
-        M_sh = rr.m;
-        nan_sh = rr.nan;
-      }
-      __syncthreads();
-      const float M = M_sh;
-      double s = 0.0, s2 = 0.0;
-      if (M > -INFINITY)
-        for (unsigned b = tid; b < G; b += kTpb) {
-          const StatPartial* q = parts + b;
-          const float qm = __ldcg(&q->m);
-          if (qm == -INFINITY) continue;
-          const double e = (double)expf(qm - M);
-          s += (double)__ldcg(&q->s) * e;
-          s2 += (double)__ldcg(&q->s2) * e * e;
-        }
-      s = block_sum_f64(s);
-      s2 = block_sum_f64(s2);
-      if (tid == 0) {
-        stat_sh[0] = (double)M + log(s);
-        stat_sh[1] = s * s / s2;
-        stat_sh[2] = (double)M;
-        if (nan_sh) record_status(&a.ctl->status, PPL_ENAN);
-        else if (!(M > -INFINITY)) record_status(&a.ctl->status, PPL_EEMPTY);
-      }
-      __syncthreads();
-    }
-    const double lse = stat_sh[0], ess = stat_sh[1];
-    const float M = (float)stat_sh[2];
-    const bool resample = ess < 0.5 * (double)N;
-    if (blockIdx.x == 0 && tid == 0) {
-      a.ess[t - 1] = ess;
-      a.resampled[t - 1] = resample ? 1 : 0;
-    }
-    last_lse = lse;
-    last_resampled = resample;
-    if (!resample) continue;
-    logz_acc += lse - log_n;
-
-    // 1. this thread's sum of fixed-point weights, then the block's exclusive scan
-    uint64_t own = 0;
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-      if (i0 + r < N) own = sat_add(own, quantize(lw[r], M, scale));
-    uint64_t inc = own;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint64_t v = __shfl_up_sync(0xffffffffu, inc, o);
-      if (lane >= o) inc = sat_add(inc, v);
-    }
-    if (lane == 31) warp_tot[warp] = inc;
     __syncthreads();
-    uint64_t texcl = inc - own, btot = 0;
-#pragma unroll
-    for (int w = 0; w < kTpb / 32; ++w) {
-      if (w < warp) texcl = sat_add(texcl, warp_tot[w]);
-      btot = sat_add(btot, warp_tot[w]);
-    }
-    if (tid == 0) a.bsum[blockIdx.x] = btot;
-    // the state goes to global memory for the gather
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-      if (i0 + r < N) a.xbuf[i0 + r] = x[r];
-    if (!grid_barrier(a.ctl, G)) return;
-    // 2. the grid's exclusive prefix of this block and the total T
-    uint64_t bexcl = 0, T = 0;
-    {
-      uint64_t be = 0, tt = 0;
-      for (unsigned b = tid; b < G; b += kTpb) {
-        const uint64_t v = __ldcg(a.bsum + b);
-        tt = sat_add(tt, v);
-        if (b < blockIdx.x) be = sat_add(be, v);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        be = sat_add(be, __shfl_xor_sync(0xffffffffu, be, o));
-        tt = sat_add(tt, __shfl_xor_sync(0xffffffffu, tt, o));
-      }
-      if (lane == 0) {
-        red[0][warp] = be;
-        red[1][warp] = tt;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int w = 0; w < kTpb / 32; ++w) {
-        bexcl = sat_add(bexcl, red[0][w]);
-        T = sat_add(T, red[1][w]);
-      }
-      __syncthreads();
-    }
-    if (T == 0 || T > (1ull << 61)) {  // every block sees the same T and leaves here
-      if (blockIdx.x == 0 && tid == 0)
-        record_status(&a.ctl->status, T == 0 ? PPL_EEMPTY : PPL_EINVAL);
-      return;
-    }
-    // 3. inclusive prefix sums C_i (the weights are recomputed: same values)
-    {
-      uint64_t run = sat_add(bexcl, texcl);
+    const float bm = warp_max(sh_max[lane]);
+    float ts = 0.0f, ts2 = 0.0f;
+    if (bm > -INFINITY) {
 #pragma unroll
       for (int r = 0; r < R; ++r)
-        if (i0 + r < N) {
-          run = sat_add(run, quantize(lw[r], M, scale));
-          a.C[i0 + r] = run;
+        if (i0 + r < N && lw[r] > -INFINITY) {
+          const float ex = expf(lw[r] - bm);
+          ts += ex;
+          ts2 = fmaf(ex, ex, ts2);
         }
     }
-    if (!grid_barrier(a.ctl, G)) return;
-    // 4. systematic positions u + k stride and their ancestors a_k = min{j : C_j > u + k stride}
-    const uint64_t stride = T / (uint64_t)N;
-    const uint32_t w0 = philox_block(a.seed, 0, 0, (uint32_t)t, kResample, 0).x;
-    const uint64_t offset =
-        (__umul64hi((uint64_t)w0, stride) << 32) | (((uint64_t)w0 * stride) >> 32);
-    const int64_t k_last = (base + kTpb * R < N ? base + kTpb * R : N) - 1;
-    if (warp < 2) {
-      const int64_t k = warp == 0 ? base : k_last;
-      const int64_t j = warp_upper_bound<true>(a.C, 0, N, offset + (uint64_t)k * stride, lane);
-      if (lane == 0) bound_sh[warp] = j < N - 1 ? j : N - 1;
-    }
+    ts = warp_sum(ts);
+    ts2 = warp_sum(ts2);
+    if (lane == 0) sh_s[warp] = make_float2(ts, ts2);
     __syncthreads();
-    const int64_t jlo = bound_sh[0], jhi = bound_sh[1];
-    const int64_t span = jhi - jlo + 1;
-    const bool staged = span <= kSmcSmem;
-    if (staged)
-      for (int64_t j = tid; j < span; j += kTpb) sC[j] = __ldcg(a.C + jlo + j);
-    __syncthreads();
-    int64_t lo = 0;  // ancestors are non-decreasing in k: each search starts at the last
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int64_t k = i0 + r;
-      if (k < N) {
-        const uint64_t pk = offset + (uint64_t)k * stride;
-        int64_t hi = span;
-        if (staged) {
-          while (lo < hi) {
-            const int64_t mid = lo + ((hi - lo) >> 1);
-            if (sC[mid] > pk) hi = mid;
-            else lo = mid + 1;
-          }
-        } else {
-          while (lo < hi) {
-            const int64_t mid = lo + ((hi - lo) >> 1);
-            if (__ldcg(a.C + jlo + mid) > pk) hi = mid;
-            else lo = mid + 1;
-          }
-        }
-        x[r] = __ldcg(a.xbuf + jlo + (lo < span ? lo : span - 1));
-        lw[r] = 0.0f;
+    if (warp == 0) {
+      const float bs = warp_sum(sh_s[lane].x), bs2 = warp_sum(sh_s[lane].y);
+      const int bn = __any_sync(0xffffffffu, sh_nan[lane]);
+      if (lane == 0) {
+        SmcPart q;
+        q.m = bm;
+        q.s = bs;
+        q.s2 = bs2;
+        q.nan = bn;
+        *reinterpret_cast<float4*>(a.parts + blockIdx.x) = *reinterpret_cast<const float4*>(&q);
       }
     }
-    __syncthreads();  // sC and bound_sh are reused by the next resampling step
+    // barrier 1: the last block merges all partials in a fixed order and
+    // publishes the maximum and the decision in the release word
+    const bool ok1 = grid_sync<true>(ctl, G, ++e, &rel, [&]() -> unsigned long long {
+      SmcPart q;
+      if ((unsigned)tid < G) {
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(a.parts + tid));
+        q = *reinterpret_cast<const SmcPart*>(&v);
+      } else {
+        q.m = -INFINITY;
+        q.s = q.s2 = 0.0f;
+        q.nan = 0;
+      }
+      const float gm = warp_max(q.m);
+      const int gn = __any_sync(0xffffffffu, q.nan);
+      if (lane == 0) {
+        j_max[warp] = gm;
+        j_nan[warp] = gn;
+      }
+      __syncthreads();
+      const float M = warp_max(j_max[lane]);
+      const int any_nan = __any_sync(0xffffffffu, j_nan[lane]);
+      float2 Ss = make_float2(0.0f, 0.0f), Ss2 = make_float2(0.0f, 0.0f);
+      if (M > -INFINITY && q.m > -INFINITY) {
+        const float ex = expf(q.m - M);
+        Ss = df_prod(q.s, ex);
+        Ss2 = df_prod(q.s2, ex * ex);
+      }
+      Ss = df_warp_sum(Ss);
+      Ss2 = df_warp_sum(Ss2);
+      if (lane == 0) {
+        j_s[warp] = Ss;
+        j_s2[warp] = Ss2;
+      }
+      __syncthreads();
+      unsigned long long payload = 0;
+      if (warp == 0) {
+        Ss = df_warp_sum(j_s[lane]);
+        Ss2 = df_warp_sum(j_s2[lane]);
+        if (lane == 0) {
+          // ESS = S^2 / S2 < N / 2  <=>  S^2 - (N / 2) S2 < 0, in double-float
+          const float2 lhs = df_mul(Ss, Ss), rhs = df_mul(make_float2(half_n, 0.0f), Ss2);
+          const bool bad = any_nan || !(M > -INFINITY);
+          const bool res =
+              !bad && __fadd_rn(__fsub_rn(lhs.x, rhs.x), __fsub_rn(lhs.y, rhs.y)) < 0.0f;
+          if (any_nan) record_status(&ctl->status, PPL_ENAN);
+          else if (bad) record_status(&ctl->status, PPL_EEMPTY);
+          SmcStep st;
+          st.M = M;
+          st.s_hi = Ss.x;
+          st.s_lo = Ss.y;
+          st.s2_hi = Ss2.x;
+          st.s2_lo = Ss2.y;
+          st.flag = res ? 1 : 0;
+          st.pad[0] = st.pad[1] = 0;
+          a.stash[t - 1] = st;
+          payload = ((unsigned long long)bad << 33) | ((unsigned long long)res << 32) |
+                    (unsigned long long)__float_as_uint(M);
+        }
+      }
+      return payload;
+    }, [] {});
+    if (!ok1) return;
+    const unsigned long long r1 = rel;
+    if ((r1 >> 33) & 1) return;  // a NaN or no finite weight: every block leaves
+    if (!((r1 >> 32) & 1)) continue;
+    const float M = __uint_as_float((uint32_t)r1);
+
+    // 1. this thread's fixed-point weights and states (kept in shared memory in
+    // particle order) and their sum, then the block's exclusive scan
+    uint64_t own = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const uint64_t q = i0 + r < N ? quantize(lw[r], M, scale) : 0ull;
+      sA[tid * R + r] = q;
+      sX[tid * R + r] = x[r];
+      own = sat_add(own, q);
+    }
+    const uint64_t inc = warp_scan_u64(own, lane);
+    if (lane == 31) sh_tot[warp] = inc;
+    __syncthreads();
+    uint64_t texcl, btot;
+    {
+      const uint64_t v = sh_tot[lane], wi = warp_scan_u64(v, lane);
+      texcl = sat_add(__shfl_sync(0xffffffffu, wi - v, warp), inc - own);
+      btot = __shfl_sync(0xffffffffu, wi, 31);
+    }
+    if (tid == 0) a.bsum[blockIdx.x] = btot;
+    // barrier 2: the last block scans the block totals, draws the systematic
+    // offset u (stride = floor(T / N)) and gives every block b the first output
+    // whose ancestor it holds, K_b = cnt(C at the block's start), where
+    // cnt(c) = #{k >= 0 : u + k stride < c}
+    const bool ok2 = grid_sync<true>(ctl, G, ++e, &rel, [&]() -> unsigned long long {
+      const uint64_t v = (unsigned)tid < G ? __ldcg(a.bsum + tid) : 0ull;
+      const uint64_t wi = warp_scan_u64(v, lane);
+      if (lane == 31) j_tot[warp] = wi;
+      __syncthreads();
+      const uint64_t jv = j_tot[lane], ji = warp_scan_u64(jv, lane);
+      const uint64_t ex = sat_add(__shfl_sync(0xffffffffu, ji - jv, warp), wi - v);
+      const uint64_t T = __shfl_sync(0xffffffffu, ji, 31);
+      const bool valid = T >= (uint64_t)N && T <= (1ull << 61);
+      if (tid == 0) {
+        const uint64_t stride = valid ? T / (uint64_t)N : 0;
+        const uint64_t w0 = resample_word;
+        if (!valid) record_status(&ctl->status, T == 0 ? PPL_EEMPTY : PPL_EINVAL);
+        j_view[0] = stride;
+        j_view[1] = (__umul64hi(w0, stride) << 32) | ((w0 * stride) >> 32);
+        ctl->total = T;
+        ctl->stride = j_view[0];
+        ctl->offset = j_view[1];
+        a.kstart[G] = N;
+      }
+      __syncthreads();
+      if (valid && (unsigned)tid < G) {
+        const uint64_t stride = j_view[0], u = j_view[1];
+        a.bexcl[tid] = ex;
+        a.kstart[tid] = ex <= u ? 0 : (int64_t)std::min<uint64_t>(ceil_div_small(ex - u, stride), (uint64_t)N);
+      }
+      return 0ull;
+    }, [&] {
+      view[0] = __ldcg(&ctl->total);
+      view[1] = __ldcg(&ctl->stride);
+      view[2] = __ldcg(&ctl->offset);
+      view[3] = __ldcg(a.bexcl + blockIdx.x);
+      view[4] = (uint64_t)__ldcg(a.kstart + blockIdx.x);
+      view[5] = (uint64_t)__ldcg(a.kstart + blockIdx.x + 1);
+    });
+    if (!ok2) return;
+    const uint64_t T = view[0];
+    if (T < (uint64_t)N || T > (1ull << 61)) return;  // every block sees the same T and leaves
+    // 2. systematic resampling of this block's outputs k in [K_b, K_b+1), whose
+    // ancestors a_k = min{j : C_j > u + k stride} are all in this block: with
+    // A_i the block-local inclusive prefix sums and B_j = u + (K_b + j) stride
+    // - C_start, a_k is the number of A's not above B_j, i.e. B_j's place in
+    // the merge of the two sorted lists (ties: A first).  The merge is cut
+    // into equal slices, one per thread (merge path: Green, McColl, Bader,
+    // "GPU merge path", ICS 2012); the outputs are assembled in shared memory
+    // and stored to global memory whole.
+    const uint64_t stride = view[1], offset = view[2], cstart = view[3];
+    const int64_t Kb = (int64_t)view[4], nB = (int64_t)view[5] - Kb;
+    {
+      uint64_t run = texcl;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        run += sA[tid * R + r];
+        sA[tid * R + r] = run;
+      }
+    }
+    __syncthreads();
+    {
+      const int nA = (int)P, nBi = (int)nB;
+      const int64_t L = (int64_t)nA + nB;
+      const int d0 = (int)(L * tid / kSmcTpb), d1 = (int)(L * (tid + 1) / kSmcTpb);
+      // B_j relative to the block start (>= 0: the outputs from K_b on lie at or past it)
+      const uint64_t b0 = offset + (uint64_t)Kb * stride - cstart;
+      int lo = d0 > nBi ? d0 - nBi : 0, hi = d0 < nA ? d0 : nA;
+      while (lo < hi) {  // the A's among the first d0 merged items
+        const int mid = (lo + hi) >> 1;
+        if (sA[mid] <= b0 + (uint64_t)(d0 - 1 - mid) * stride) lo = mid + 1;
+        else hi = mid;
+      }
+      int i = lo, j = d0 - lo;
+      uint64_t bj = b0 + (uint64_t)j * stride;
+      uint64_t ai = i < nA ? sA[i] : ~0ull;
+      for (int s = d0; s < d1; ++s) {
+        if (j >= nBi || ai <= bj) {
+          ++i;
+          ai = i < nA ? sA[i] : ~0ull;
+        } else {  // output K_b + j: ancestor i (A_i > B_j, so i < nA)
+          const float v = sX[i < nA ? i : nA - 1];
+          if (j < kSmcOut) sx[j] = v;
+          else a.xbuf[Kb + j] = v;  // beyond the staging area: straight to global memory
+          ++j;
+          bj += stride;
+        }
+      }
+    }
+    __syncthreads();
+    {
+      const int64_t n_staged = nB < kSmcOut ? nB : kSmcOut;
+      for (int64_t j = tid; j < n_staged; j += kSmcTpb) a.xbuf[Kb + j] = sx[j];
+    }
+    if (!grid_sync<false>(ctl, G, ++e, &rel, [] { return 0ull; }, [] {})) return;
+    // 3. the new population: this thread's outputs are i0 .. i0 + R - 1
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (i0 + r < N) x[r] = __ldcg(a.xbuf + i0 + r);
+      lw[r] = 0.0f;
+    }
   }
-  // evidence: accumulated normalisers plus the unnormalised last step
-  if (blockIdx.x == 0 && tid == 0)
-    a.logz[0] = logz_acc + (last_resampled ? 0.0 : last_lse - log_n);
+  // evidence and ESS of every step, in FP64, by block 0 after the last step:
+  // log Z = sum over resampling steps of (lse_t - log N), plus lse_T - log N
+  // when the last step did not resample (its weights are carried unnormalised)
+  if (blockIdx.x == 0) {
+    const double log_n = log((double)N);
+    double z = 0.0;
+    for (int t = tid; t < a.T; t += kSmcTpb) {
+      const float4 h0 = __ldcg(reinterpret_cast<const float4*>(a.stash + t));
+      const float4 h1 = __ldcg(reinterpret_cast<const float4*>(a.stash + t) + 1);
+      const double S1 = (double)h0.y + (double)h0.z;
+      const double S2 = (double)h0.w + (double)h1.x;
+      const int flag = __float_as_int(h1.y);
+      const double lse = (double)h0.x + log(S1);
+      a.ess[t] = S1 * S1 / S2;
+      a.resampled[t] = flag;
+      if (flag || t == a.T - 1) z += lse - log_n;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+    if (lane == 0) sh_z[warp] = z;
+    __syncthreads();
+    if (warp == 0) {
+      z = sh_z[lane];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) z += __shfl_xor_sync(0xffffffffu, z, o);
+      if (lane == 0) a.logz[0] = z;
+    }
+  }
 #pragma unroll
   for (int r = 0; r < R; ++r)
     if (i0 + r < N) {
@@ -321,29 +531,34 @@ __global__ void __launch_bounds__(kTpb, 4) smc_persistent_kernel(SmcArgs a) {
     }
 }
 
-size_t smc_run_workspace(int64_t N) {
-  const size_t grid = (size_t)kMaxBlocks;
-  return 5 * 256 + grid * (2 * sizeof(StatPartial) + 8) + (size_t)N * (8 + 4);
+size_t smc_run_workspace(int64_t N, int64_t T) {
+  return 8 * 256 + (size_t)kSmcMaxGrid * (sizeof(SmcPart) + 3 * 8) + 8 +
+         (size_t)std::max<int64_t>(T, 0) * sizeof(SmcStep) + (size_t)N * 4;
 }
 
 template <int R>
-static cudaError_t launch_r(SmcArgs& a, int64_t max_blocks, cudaStream_t s, bool* fits) {
-  const int64_t grid = (a.N + (int64_t)kTpb * R - 1) / ((int64_t)kTpb * R);
-  int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smc_persistent_kernel<R>,
-                                                                kTpb, 0);
+static cudaError_t launch_r(SmcArgs& a, cudaStream_t s, bool* fits) {
+  const int64_t grid = (a.N + (int64_t)kSmcTpb * R - 1) / ((int64_t)kSmcTpb * R);
+  constexpr size_t dyn = (size_t)R * kSmcTpb * (8 + 4) + (size_t)kSmcOut * 4;
+  cudaError_t e = cudaFuncSetAttribute(smc_persistent_kernel<R>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (e != cudaSuccess) return e;
-  *fits = grid <= std::min<int64_t>((int64_t)num_sms() * per_sm, max_blocks);
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, smc_persistent_kernel<R>, kSmcTpb,
+                                                    dyn);
+  if (e != cudaSuccess) return e;
+  *fits = grid <= std::min<int64_t>((int64_t)num_sms() * per_sm, kSmcMaxGrid);
   if (!*fits) return cudaSuccess;
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel((const void*)smc_persistent_kernel<R>, dim3((unsigned)grid),
-                                     dim3(kTpb), args, 0, s);
+                                     dim3(kSmcTpb), args, dyn, s);
 }
 
 cudaError_t launch_smc_persistent(const LgssmParams& p, const float* y, int32_t T, uint64_t seed,
                                   int64_t N, float* x_out, float* lw_out, double* logz,
                                   int32_t* resampled, double* ess, char* ws, size_t ws_bytes,
                                   int32_t** status_out, cudaStream_t s) {
+  if (T < 1 || T > (1 << 27)) return cudaErrorInvalidValue;  // barrier numbers fit 30 bits
   SmcArgs a;
   a.p = p;
   a.y = y;
@@ -355,7 +570,6 @@ cudaError_t launch_smc_persistent(const LgssmParams& p, const float* y, int32_t 
   a.logz = logz;
   a.resampled = resampled;
   a.ess = ess;
-  const int64_t max_blocks = kMaxBlocks;
   size_t off = 0;
   auto take = [&](size_t bytes) {
     char* q = ws + off;
@@ -363,9 +577,11 @@ cudaError_t launch_smc_persistent(const LgssmParams& p, const float* y, int32_t 
     return q;
   };
   a.ctl = reinterpret_cast<SmcCtl*>(take(sizeof(SmcCtl)));
-  a.parts = reinterpret_cast<StatPartial*>(take(2 * (size_t)max_blocks * sizeof(StatPartial)));
-  a.bsum = reinterpret_cast<uint64_t*>(take((size_t)max_blocks * 8));
-  a.C = reinterpret_cast<uint64_t*>(take((size_t)N * 8));
+  a.parts = reinterpret_cast<SmcPart*>(take((size_t)kSmcMaxGrid * sizeof(SmcPart)));
+  a.bsum = reinterpret_cast<uint64_t*>(take((size_t)kSmcMaxGrid * 8));
+  a.bexcl = reinterpret_cast<uint64_t*>(take((size_t)kSmcMaxGrid * 8));
+  a.kstart = reinterpret_cast<int64_t*>(take(((size_t)kSmcMaxGrid + 1) * 8));
+  a.stash = reinterpret_cast<SmcStep*>(take((size_t)T * sizeof(SmcStep)));
   a.xbuf = reinterpret_cast<float*>(take((size_t)N * 4));
   if (off > ws_bytes) return cudaErrorInvalidValue;
   *status_out = &a.ctl->status;
@@ -373,10 +589,14 @@ cudaError_t launch_smc_persistent(const LgssmParams& p, const float* y, int32_t 
   if (e != cudaSuccess) return e;
   // fewest particles per thread whose grid is resident at once
   bool fits = false;
-  if ((e = launch_r<1>(a, max_blocks, s, &fits)) != cudaSuccess || fits) return e;
-  if ((e = launch_r<2>(a, max_blocks, s, &fits)) != cudaSuccess || fits) return e;
-  if ((e = launch_r<4>(a, max_blocks, s, &fits)) != cudaSuccess || fits) return e;
-  if ((e = launch_r<8>(a, max_blocks, s, &fits)) != cudaSuccess || fits) return e;
+  if ((e = launch_r<1>(a, s, &fits)) != cudaSuccess || fits) return e;
+  if ((e = launch_r<2>(a, s, &fits)) != cudaSuccess || fits) return e;
+  if ((e = launch_r<3>(a, s, &fits)) != cudaSuccess || fits) return e;
+  if ((e = launch_r<4>(a, s, &fits)) != cudaSuccess || fits) return e;
+  if ((e = launch_r<5>(a, s, &fits)) != cudaSuccess || fits) return e;
+  if ((e = launch_r<6>(a, s, &fits)) != cudaSuccess || fits) return e;
+  if ((e = launch_r<7>(a, s, &fits)) != cudaSuccess || fits) return e;
+  if ((e = launch_r<8>(a, s, &fits)) != cudaSuccess || fits) return e;
   return cudaErrorInvalidValue;  // more particles than resident threads can hold
 }
 
