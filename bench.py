@@ -53,6 +53,8 @@ def parse():
                     help="skip the state-space, batched and learned-proposal workloads")
     ap.add_argument("--particles", type=int, default=N_PARTICLES,
                     help="particles per step (smaller cases for profiling only)")
+    ap.add_argument("--config", choices=["smc", "batched", "learned"],
+                    help="run only this secondary workload and print its line (profiling)")
     return ap.parse_args()
 
 
@@ -537,10 +539,23 @@ def run_ours(args):
     return 0
 
 
+def run_config(args):
+    import torch
+
+    import paper_2010_08454_gb300.binding as ppl
+    torch.cuda.set_device(0)
+    ppl.lib()
+    fn = {"smc": bench_smc, "batched": bench_batched, "learned": bench_learned}[args.config]
+    print(json.dumps({"config": args.config, "result": fn(torch, ppl)}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config:
+        return run_config(args)
     return run_ours(args)
 
 

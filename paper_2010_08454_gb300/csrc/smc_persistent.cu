@@ -22,7 +22,7 @@
 // resident at once (or fails to launch).
 #include <algorithm>
 
-#include "fixedpoint.cuh"
+#include "gridsync.cuh"
 #include "kernels.h"
 #include "rng.cuh"
 
@@ -30,7 +30,6 @@ namespace ppl {
 
 constexpr int kSmcTpb = 1024;          // threads of a block: one block per SM
 constexpr int kSmcWarps = kSmcTpb / 32;
-constexpr int kSmcSpin = 1 << 22;      // bound of one barrier wait (polls)
 constexpr int kSmcMaxGrid = kSmcTpb;   // the merging block holds one partial per thread
 constexpr int kSmcOut = 24576;         // outputs a block stages in shared memory
 
@@ -49,19 +48,14 @@ struct __align__(16) SmcStep {
   int32_t flag, pad[2];
 };
 
-// Control block at offset 0 of the workspace.  Line 0: the status (first, where
-// ppl_workspace_status reads it) and the arrival counter; line 1: the release
-// word and what the last block of barrier 2 publishes with it.  The release
-// word is (barrier number << 34) | payload; barrier 1's payload is
-// bad << 33 | resample << 32 | bits of M.
+// Control block at offset 0 of the workspace: the status word (first, where
+// ppl_workspace_status reads it) on its own line, then the barrier words.
+// Barrier 1's payload in the release word is bad << 33 | resample << 32 |
+// bits of M; barrier 2 publishes T, the stride and u.
 struct __align__(128) SmcCtl {
   int32_t status;
-  int32_t pad0;
-  unsigned long long arrive;  // arrivals so far: barrier e is complete at e * grid
-  char pad1[112];
-  unsigned long long release;
-  unsigned long long pad2;
-  unsigned long long total, stride, offset;  // T, floor(T / N), u
+  int32_t pad[31];
+  GridCtl g;
 };
 
 // Double-float arithmetic (pairs hi + lo, |lo| <= ulp(hi) / 2): Knuth's
@@ -92,102 +86,6 @@ __device__ __forceinline__ float2 df_warp_sum(float2 v) {
                               __shfl_xor_sync(0xffffffffu, v.y, o)));
   return v;
 }
-// Inclusive warp scan of saturating 64-bit sums.
-__device__ __forceinline__ uint64_t warp_scan_u64(uint64_t v, int lane) {
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint64_t u = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v = sat_add(v, u);
-  }
-  return v;
-}
-
-// The leading 24 bits of v > 0 as an FP32 number (relative error below
-// 2^-23), through 32-bit conversions only.
-__device__ __forceinline__ float lead_f32(uint64_t v) {
-  const int sh = max(0, 40 - __clzll(v));  // v >> sh < 2^24
-  return __fmul_rn(__uint2float_rn((uint32_t)(v >> sh)), __int_as_float((127 + sh) << 23));
-}
-
-// ceil(num / den) for 0 < num, den < 2^62 and a quotient below 2^22: an FP32
-// estimate (relative error below 2^-21, so within two of the quotient), then
-// exact integer corrections.
-__device__ __forceinline__ uint64_t ceil_div_small(uint64_t num, uint64_t den) {
-  uint64_t k = __float2uint_rz(__fdividef(lead_f32(num), lead_f32(den)));
-  for (int i = 0; i < 4 && k * den < num; ++i) ++k;
-  for (int i = 0; i < 4 && k > 0 && (k - 1) * den >= num; ++i) --k;
-  if (k * den < num || (k > 0 && (k - 1) * den >= num)) k = (num + den - 1) / den;  // never taken
-  return k;
-}
-
-__device__ __forceinline__ unsigned long long atom_add_acq_rel(unsigned long long* p,
-                                                               unsigned long long v) {
-  unsigned long long old;
-  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;"
-               : "=l"(old)
-               : "l"(p), "l"(v)
-               : "memory");
-  return old;
-}
-
-// Grid barrier number e (1-based; every block counts its own).  After a block
-// barrier, thread 0 arrives with an acquire-release atomic.  Without a job the
-// others poll the arrival count.  With one, the block whose arrival completes
-// the count runs `job` with all its threads (thread 0's return value is the
-// payload) and releases the others, which poll the release word; every block
-// finds the release word in *rel.  Thread 0 then runs `after` before the
-// closing block barrier.  Returns false when the kernel must stop.
-template <bool kJob, class Job, class After>
-__device__ __forceinline__ bool grid_sync(SmcCtl* ctl, unsigned G, unsigned long long e,
-                                          unsigned long long* rel, Job&& job, After&& after) {
-  __shared__ int role;  // 1: ran the job, 0: released, -1: stop
-  __syncthreads();      // the block's writes precede thread 0's release
-  if (threadIdx.x == 0) {
-    const unsigned long long target = e * G;
-    const unsigned long long old = atom_add_acq_rel(&ctl->arrive, 1ull);
-    int r = 0;
-    if (old == target - 1) {
-      r = kJob ? 1 : 0;
-    } else {
-      const uint64_t* word =
-          reinterpret_cast<const uint64_t*>(kJob ? &ctl->release : &ctl->arrive);
-      int spins = 0;
-      for (;;) {
-        const unsigned long long v = ld_acquire_u64(word);
-        if (kJob ? (v >> 34) >= e : v >= target) {
-          if (kJob) *rel = v;
-          break;
-        }
-        if ((spins & 15) == 15 && ld_volatile_i32(&ctl->status) != 0) {  // another block gave up
-          r = -1;
-          break;
-        }
-        if (++spins > kSmcSpin) {
-          record_status(&ctl->status, PPL_ETIMEOUT);
-          r = -1;
-          break;
-        }
-        if (spins > 32) __nanosleep(32);
-      }
-    }
-    role = r;
-  }
-  __syncthreads();
-  const int r = role;
-  if (r == 1) {
-    const unsigned long long payload = job();
-    __syncthreads();  // the job's writes precede the release
-    if (threadIdx.x == 0) {
-      const unsigned long long v = (e << 34) | payload;
-      st_release_u64(reinterpret_cast<uint64_t*>(&ctl->release), v);
-      *rel = v;
-    }
-  }
-  if (r >= 0 && threadIdx.x == 0) after();
-  __syncthreads();
-  return r >= 0;
-}
-
 struct SmcArgs {
   LgssmParams p;
   const float* y;  // [T]
@@ -308,7 +206,7 @@ __global__ void __launch_bounds__(kSmcTpb, 1) smc_persistent_kernel(SmcArgs a) {
     }
     // barrier 1: the last block merges all partials in a fixed order and
     // publishes the maximum and the decision in the release word
-    const bool ok1 = grid_sync<true>(ctl, G, ++e, &rel, [&]() -> unsigned long long {
+    const bool ok1 = grid_sync<true>(&ctl->g, &ctl->status, G, ++e, &rel, [&]() -> unsigned long long {
       SmcPart q;
       if ((unsigned)tid < G) {
         const float4 v = __ldcg(reinterpret_cast<const float4*>(a.parts + tid));
@@ -397,7 +295,7 @@ __global__ void __launch_bounds__(kSmcTpb, 1) smc_persistent_kernel(SmcArgs a) {
     // offset u (stride = floor(T / N)) and gives every block b the first output
     // whose ancestor it holds, K_b = cnt(C at the block's start), where
     // cnt(c) = #{k >= 0 : u + k stride < c}
-    const bool ok2 = grid_sync<true>(ctl, G, ++e, &rel, [&]() -> unsigned long long {
+    const bool ok2 = grid_sync<true>(&ctl->g, &ctl->status, G, ++e, &rel, [&]() -> unsigned long long {
       const uint64_t v = (unsigned)tid < G ? __ldcg(a.bsum + tid) : 0ull;
       const uint64_t wi = warp_scan_u64(v, lane);
       if (lane == 31) j_tot[warp] = wi;
@@ -412,22 +310,22 @@ __global__ void __launch_bounds__(kSmcTpb, 1) smc_persistent_kernel(SmcArgs a) {
         if (!valid) record_status(&ctl->status, T == 0 ? PPL_EEMPTY : PPL_EINVAL);
         j_view[0] = stride;
         j_view[1] = (__umul64hi(w0, stride) << 32) | ((w0 * stride) >> 32);
-        ctl->total = T;
-        ctl->stride = j_view[0];
-        ctl->offset = j_view[1];
+        ctl->g.total = T;
+        ctl->g.stride = j_view[0];
+        ctl->g.offset = j_view[1];
         a.kstart[G] = N;
       }
       __syncthreads();
       if (valid && (unsigned)tid < G) {
         const uint64_t stride = j_view[0], u = j_view[1];
         a.bexcl[tid] = ex;
-        a.kstart[tid] = ex <= u ? 0 : (int64_t)std::min<uint64_t>(ceil_div_small(ex - u, stride), (uint64_t)N);
+        a.kstart[tid] = positions_below(ex, u, stride, N);
       }
       return 0ull;
     }, [&] {
-      view[0] = __ldcg(&ctl->total);
-      view[1] = __ldcg(&ctl->stride);
-      view[2] = __ldcg(&ctl->offset);
+      view[0] = __ldcg(&ctl->g.total);
+      view[1] = __ldcg(&ctl->g.stride);
+      view[2] = __ldcg(&ctl->g.offset);
       view[3] = __ldcg(a.bexcl + blockIdx.x);
       view[4] = (uint64_t)__ldcg(a.kstart + blockIdx.x);
       view[5] = (uint64_t)__ldcg(a.kstart + blockIdx.x + 1);
@@ -487,7 +385,7 @@ __global__ void __launch_bounds__(kSmcTpb, 1) smc_persistent_kernel(SmcArgs a) {
       const int64_t n_staged = nB < kSmcOut ? nB : kSmcOut;
       for (int64_t j = tid; j < n_staged; j += kSmcTpb) a.xbuf[Kb + j] = sx[j];
     }
-    if (!grid_sync<false>(ctl, G, ++e, &rel, [] { return 0ull; }, [] {})) return;
+    if (!grid_sync<false>(&ctl->g, &ctl->status, G, ++e, &rel, [] { return 0ull; }, [] {})) return;
     // 3. the new population: this thread's outputs are i0 .. i0 + R - 1
 #pragma unroll
     for (int r = 0; r < R; ++r) {

@@ -79,33 +79,82 @@ __host__ __device__ constexpr size_t trace_smem_bytes() {
   return (sizeof(TraceSmem<PPT>) + 15) / 16 * 16;
 }
 
+// Paired FP32 arithmetic (PTX f32x2, sm_100 and later): two lanes of IEEE
+// single precision in one 64-bit register, each half rounded exactly as the
+// scalar instruction would round it.  One instruction does the work of two,
+// which halves the issue slots of the Horner chain below.
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+  unsigned long long v;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(v) : "f"(lo), "f"(hi));
+  return v;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long v) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+  return make_float2(lo, hi);
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+
 // ss += sum over the staged points of (y - f(x))^2, f by Horner's rule over NC
-// coefficients, for PPT traces at once.  Inner sums of 16 points are combined
-// by a compensated (Kahan) sum.
+// coefficients, for PPT traces at once (in pairs when PPT is even: the
+// results are those of the scalar chain, bit for bit).  Inner sums of 16
+// points are combined by a compensated (Kahan) sum.
 template <int PPT, int NC>
 __device__ __forceinline__ void accumulate_nc(const float2* sdata, int len,
                                               const float (&c)[PPT][kMaxCoef], float (&ss)[PPT],
                                               float (&comp)[PPT]) {
-  int l = 0;
-  while (l < len) {
-    const int n = (len - l) < 16 ? (len - l) : 16;
-    float part[PPT];
+  if constexpr (PPT % 2 == 0) {
+    constexpr int NP = PPT / 2;
+    unsigned long long cc[NP][NC];
 #pragma unroll
-    for (int q = 0; q < PPT; ++q) part[q] = 0.0f;
-    if (n == 16) {
+    for (int p = 0; p < NP; ++p)
+#pragma unroll
+      for (int k = 0; k < NC; ++k) cc[p][k] = f2_pack(c[2 * p][k], c[2 * p + 1][k]);
+    int l = 0;
+    while (l < len) {
+      const int n = (len - l) < 16 ? (len - l) : 16;
+      unsigned long long part[NP];
+#pragma unroll
+      for (int p = 0; p < NP; ++p) part[p] = 0ull;  // +0.0f in both halves
 #pragma unroll 4
-      for (int j = 0; j < 16; ++j) {
+      for (int j = 0; j < n; ++j) {
         const float2 d = sdata[l + j];
+        const unsigned long long xx = f2_pack(d.x, d.x), yy = f2_pack(d.y, d.y);
 #pragma unroll
-        for (int q = 0; q < PPT; ++q) {
-          float f = c[q][NC - 1];
+        for (int p = 0; p < NP; ++p) {
+          unsigned long long f = cc[p][NC - 1];
 #pragma unroll
-          for (int k = NC - 2; k >= 0; --k) f = fmaf(f, d.x, c[q][k]);
-          const float r = d.y - f;
-          part[q] = fmaf(r, r, part[q]);
+          for (int k = NC - 2; k >= 0; --k) f = f2_fma(f, xx, cc[p][k]);
+          const unsigned long long r = f2_sub(yy, f);
+          part[p] = f2_fma(r, r, part[p]);
         }
       }
-    } else {
+#pragma unroll
+      for (int p = 0; p < NP; ++p) {
+        const float2 v = f2_unpack(part[p]);
+        kahan_add(ss[2 * p], comp[2 * p], v.x);
+        kahan_add(ss[2 * p + 1], comp[2 * p + 1], v.y);
+      }
+      l += n;
+    }
+  } else {
+    int l = 0;
+    while (l < len) {
+      const int n = (len - l) < 16 ? (len - l) : 16;
+      float part[PPT];
+#pragma unroll
+      for (int q = 0; q < PPT; ++q) part[q] = 0.0f;
+#pragma unroll 4
       for (int j = 0; j < n; ++j) {
         const float2 d = sdata[l + j];
 #pragma unroll
@@ -117,10 +166,10 @@ __device__ __forceinline__ void accumulate_nc(const float2* sdata, int len,
           part[q] = fmaf(r, r, part[q]);
         }
       }
-    }
 #pragma unroll
-    for (int q = 0; q < PPT; ++q) kahan_add(ss[q], comp[q], part[q]);
-    l += n;
+      for (int q = 0; q < PPT; ++q) kahan_add(ss[q], comp[q], part[q]);
+      l += n;
+    }
   }
 }
 
