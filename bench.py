@@ -38,7 +38,12 @@ UNIT = "traces/s"
 WORKLOAD = ("linefitting likelihood weighting, 2^24 particles x 256 points, degree "
             "uniform{2..5}, coefficients N(0,10^2), sigma 0.5; + log-sum-exp/ESS + posterior "
             "reduce + systematic resampling (64-bit fixed point) + gather of 32-byte records")
-KERNELS_PER_STEP = 5  # trace (posterior fused), scan, chunk bounds, ancestors, gather
+KERNELS_PER_STEP = 3  # trace (normalisation and posterior fused), resampling, gather
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
+# poly_trace_kernel launch on the default workload, from the full-size ncu
+# capture summarised in profiles/poly_trace_kernel_2e22x256.md; re-measure
+# whenever the kernel changes.
+TRACE_TRAFFIC_BYTES = 363008 + 542036480
 
 
 def parse():
@@ -517,7 +522,8 @@ def run_ours(args):
                    "l2": "flushed between timed steps (256 MiB write outside the events)"},
         "roofline": {"kernel": "poly_trace_kernel", "bound": "alu", "achieved": achieved,
                      "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                     "traffic": None,
+                     "traffic": TRACE_TRAFFIC_BYTES if N == N_PARTICLES else None,
+                     "traffic_unit": "bytes per launch",
                      "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {max_mhz} MHz",
                      "work": "FP32 flops of the factor: L x (2 ncoef + 1) per trace"},
         "stages_ms": {"trace": trace_ms, "posterior": float(stage[:, 1].mean()),
