@@ -58,7 +58,7 @@ def parse():
                     help="skip the state-space, batched and learned-proposal workloads")
     ap.add_argument("--particles", type=int, default=N_PARTICLES,
                     help="particles per step (smaller cases for profiling only)")
-    ap.add_argument("--config", choices=["smc", "batched", "learned"],
+    ap.add_argument("--config", choices=["smc", "batched", "learned", "suffstat"],
                     help="run only this secondary workload and print its line (profiling)")
     return ap.parse_args()
 
@@ -246,6 +246,43 @@ def bench_smc(torch, ppl, reps=5):
             "stepwise_graph": {"ms_per_filter": ms_steps, "log_z": logz_steps,
                                "gpu_launches_per_filter": 5 * T,
                                "same_particles": bool(torch.equal(out["x"], x))}}
+
+
+def bench_suffstat(torch, ppl, reps=10):
+    """The line-fitting workload (2^24 particles x 256 points) with the factor
+    from the data's sufficient statistics (a separate variant: the headline
+    counts the point-by-point FLOPs)."""
+    import numpy as np
+
+    import synth
+    N = N_PARTICLES
+    x, y = synth.poly_dataset(N_POINTS, DATA_SEED)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    model = ppl.poly_model()
+    lw = torch.empty(N, dtype=torch.float32, device="cuda")
+    parts = ppl.poly_particles(N)
+    ws = ppl.workspace(model, N, N_POINTS)
+    res = ppl.result_tensor()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    times = {}
+    for name, fn in (("suffstat", ppl.ppl_infer_is_suffstat), ("direct", ppl.ppl_infer_is_instance)):
+        def call():
+            fn(model, xd, yd, N, INFER_SEED, 0, out=res, lw_out=lw, particles_out=parts, ws=ws)
+        for _ in range(3):
+            call()
+        t = []
+        for _ in range(reps):
+            flush.fill_(1)
+            t.append(_event_ms(torch, call, 1))
+        times[name] = float(np.median(t))
+    summary = ppl.read_result(res)
+    return {"workload": "likelihood weighting, 2^24 particles x 256 points, factor from the "
+                        "sufficient statistics (one Cholesky of the 6 x 6 Gram matrix, O(d^2) "
+                        "per trace); records and log-weights written as in the headline step",
+            "metric": "particle-traces/sec", "value": N / (times["suffstat"] / 1e3),
+            "unit": "traces/s", "ms_per_launch": times["suffstat"],
+            "direct_ms_per_launch": times["direct"], "log_z": summary["log_z"],
+            "gpu_launches_per_call": 2}
 
 
 def bench_batched(torch, ppl, reps=5):
@@ -537,6 +574,7 @@ def run_ours(args):
     }
     if not args.no_configs:
         out["configs"] = {"smc_lgssm_T200_2e20": bench_smc(torch, ppl),
+                          "suffstat_linefitting_2e24x256": bench_suffstat(torch, ppl),
                           "batched_4096": bench_batched(torch, ppl),
                           "learned_proposal_1024x2e20": bench_learned(torch, ppl)}
     if not args.no_cpu_baseline:
@@ -551,7 +589,8 @@ def run_config(args):
     import paper_2010_08454_gb300.binding as ppl
     torch.cuda.set_device(0)
     ppl.lib()
-    fn = {"smc": bench_smc, "batched": bench_batched, "learned": bench_learned}[args.config]
+    fn = {"smc": bench_smc, "batched": bench_batched, "learned": bench_learned,
+          "suffstat": bench_suffstat}[args.config]
     print(json.dumps({"config": args.config, "result": fn(torch, ppl)}), flush=True)
     return 0
 

@@ -133,6 +133,23 @@ ppl_status ppl_infer_is_instance(const ppl_model* model, const ppl_data* data,
                                  ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,
                                  ppl_stream stream);
 
+/* ppl_infer_is_instance with the factor evaluated from the data's
+ * sufficient statistics instead of point by point.  The model of Fig. 1 is
+ * linear in its coefficients, so with Phi the matrix of powers x_l^j,
+ * G = Phi^T Phi = R^T R and w = R^-T Phi^T y, a trace with d coefficients has
+ * sum_l (y_l - f(x_l))^2 = (y^T y - sum_{i<d} w_i^2) + |R_d c - w_d|^2 (exact in
+ * real arithmetic; both terms are non-negative, so nothing cancels).  One
+ * small kernel forms G, R and w in FP64; each trace then costs O(d^2) instead
+ * of O(L d).  The draws, and so the traces, are those of ppl_infer_is_instance
+ * bit for bit; log-weights differ by rounding only.  When G is singular to
+ * working precision (fewer distinct points than coefficients) the point-by-
+ * point sum is used.  Same arguments and workspace as ppl_infer_is_instance. */
+ppl_status ppl_infer_is_suffstat(const ppl_model* model, const ppl_data* data,
+                                 int64_t n_particles, uint64_t seed, uint32_t instance,
+                                 ppl_is_result* out_dev, float* lw_out,
+                                 ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,
+                                 ppl_stream stream);
+
 /* Same as ppl_infer_is with the data and the result in host memory: copies x,
  * y in, runs, copies the summary out, and synchronises `stream` before it
  * returns.  The workspace must also hold the data (see ppl_workspace_size). */

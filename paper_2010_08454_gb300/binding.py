@@ -81,6 +81,10 @@ _SIGS = {
                                              ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_size_t, ctypes.c_void_p]),
+    "ppl_infer_is_suffstat": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                             ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
+                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                             ctypes.c_size_t, ctypes.c_void_p]),
     "ppl_infer_is_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
@@ -273,6 +277,24 @@ def ppl_infer_is_instance(model, x, y, n_particles, seed, instance, out=None, lw
                                      _ptr(lw_out), _ptr(particles_out), _ptr(ws), ws.numel(),
                                      _stream(stream))
     _check(st, "ppl_infer_is_instance")
+    return out
+
+
+def ppl_infer_is_suffstat(model, x, y, n_particles, seed, instance=0, out=None, lw_out=None,
+                          particles_out=None, ws=None, stream=None):
+    """ppl_infer_is_instance with the factor from the data's sufficient statistics."""
+    _dev_f32(x, "x")
+    _dev_f32(y, "y")
+    if ws is None:
+        ws = workspace(model, n_particles, x.numel(), x.device)
+    if out is None:
+        out = result_tensor(x.device)
+    data = PplData(x.data_ptr(), y.data_ptr(), x.numel())
+    st = lib().ppl_infer_is_suffstat(ctypes.byref(model), ctypes.byref(data), int(n_particles),
+                                     ctypes.c_uint64(seed), int(instance), _ptr(out),
+                                     _ptr(lw_out), _ptr(particles_out), _ptr(ws), ws.numel(),
+                                     _stream(stream))
+    _check(st, "ppl_infer_is_suffstat")
     return out
 
 

@@ -150,6 +150,30 @@ ppl_status ppl_infer_is_instance(const ppl_model* model, const ppl_data* data,
   return PPL_OK;
 }
 
+ppl_status ppl_infer_is_suffstat(const ppl_model* model, const ppl_data* data,
+                                 int64_t n_particles, uint64_t seed, uint32_t instance,
+                                 ppl_is_result* out_dev, float* lw_out,
+                                 ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,
+                                 ppl_stream stream) {
+  PolyParams p;
+  PPL_TRY(poly_params(model, &p));
+  if (!data || data->len < 0 || (data->len > 0 && (!data->x || !data->y))) return PPL_EINVAL;
+  if (n_particles < 1 || n_particles > kMaxParticles || !out_dev) return PPL_EINVAL;
+  if (particles_out && (reinterpret_cast<uintptr_t>(particles_out) & 15)) return PPL_EINVAL;
+  Ws w;
+  PPL_TRY(check_ws(ws, ws_bytes, n_particles, data->len, &w));
+  cudaStream_t s = (cudaStream_t)stream;
+  PPL_TRY(reset_ws(w, false, s));
+  PPL_TRY(cuda_status(cudaMemsetAsync(out_dev, 0, sizeof(ppl_is_result), s)));
+  // the statistics live in the scratch region, unused by likelihood weighting
+  const int d_max = p.min_deg + p.n_deg - 1 + p.coef_offset;
+  PPL_TRY(cuda_status(launch_suffstat(data->x, data->y, data->len, d_max, w.scratch(), s)));
+  PPL_TRY(cuda_status(launch_poly_trace(p, data->x, data->y, data->len, n_particles, seed,
+                                        instance, lw_out, particles_out, w.hdr(), w.partials(),
+                                        out_dev, s, w.scratch())));
+  return PPL_OK;
+}
+
 ppl_status ppl_infer_is(const ppl_model* model, const ppl_data* data, int64_t n_particles,
                         uint64_t seed, ppl_is_result* out_dev, float* lw_out,
                         ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,

@@ -74,12 +74,21 @@ __global__ void __launch_bounds__(kTpb, 3) poly_trace_kernel(
     PolyParams p, const float* __restrict__ xs, const float* __restrict__ ys, int64_t L,
     int64_t N, uint64_t seed, uint32_t instance, int chunk, float* __restrict__ lw_out,
     ppl_poly_particle* __restrict__ rec_out, WsHeader* hdr, DegPartial* parts,
-    ppl_is_result* res) {
+    ppl_is_result* res, const SuffStat* suff_g) {
   extern __shared__ __align__(16) unsigned char smem[];
   TraceSmem<PPT>& ts = *reinterpret_cast<TraceSmem<PPT>*>(smem);
   float2* sdata = reinterpret_cast<float2*>(smem + trace_smem_bytes<PPT>());
   __shared__ DegPartial run[kMaxDegrees];
+  __shared__ SuffStat suff_sh;
   const int tid = threadIdx.x;
+  // the sufficient-statistics variant: its coefficients, read once per block
+  const SuffStat* suff = nullptr;
+  if (suff_g) {
+    static_assert(sizeof(SuffStat) % 4 == 0, "copied as words");
+    for (int i = tid; i < (int)(sizeof(SuffStat) / 4); i += kTpb)
+      reinterpret_cast<int*>(&suff_sh)[i] = reinterpret_cast<const int*>(suff_g)[i];
+    suff = &suff_sh;
+  }
   const int64_t group = (int64_t)kTpb * PPT;
   const int64_t n_groups = (N + group - 1) / group;
   const bool resident = L <= chunk;
@@ -90,7 +99,7 @@ __global__ void __launch_bounds__(kTpb, 3) poly_trace_kernel(
   int nan = 0;
   for (int64_t g = blockIdx.x; g < n_groups; g += gridDim.x) {
     trace_group<PPT>(PriorDraw{p, seed, instance}, p, xs, ys, L, chunk, resident, sdata, N,
-                     g * group, lw_out, rec_out, ts);
+                     g * group, lw_out, rec_out, ts, suff);
     if (tid == 0) nan |= ts.nan;
   }
   merge_warp_partials(ts, run);
@@ -209,7 +218,7 @@ int stream_grid(int64_t N) {
 cudaError_t launch_poly_trace(const PolyParams& p, const float* x, const float* y, int64_t L,
                               int64_t N, uint64_t seed, uint32_t instance, float* lw_out,
                               ppl_poly_particle* rec_out, WsHeader* hdr, void* parts,
-                              ppl_is_result* res, cudaStream_t s) {
+                              ppl_is_result* res, cudaStream_t s, const void* suff) {
   constexpr int PPT = kTraceKernelPpt;
   const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(L, kMaxChunk));
   const size_t smem = trace_smem_bytes<PPT>() + (size_t)chunk * sizeof(float2);
@@ -227,7 +236,8 @@ cudaError_t launch_poly_trace(const PolyParams& p, const float* x, const float* 
   if (e != cudaSuccess) return e;
   const int grid = std::max(1, std::min(trace_grid(N), num_sms() * std::max(1, per_sm)));
   poly_trace_kernel<PPT><<<grid, kTpb, smem, s>>>(p, x, y, L, N, seed, instance, chunk, lw_out,
-                                                  rec_out, hdr, (DegPartial*)parts, res);
+                                                  rec_out, hdr, (DegPartial*)parts, res,
+                                                  (const SuffStat*)suff);
   return cudaGetLastError();
 }
 

@@ -21,7 +21,12 @@ size_t partials_bytes();
 cudaError_t launch_poly_trace(const PolyParams& p, const float* x, const float* y, int64_t L,
                               int64_t N, uint64_t seed, uint32_t instance, float* lw_out,
                               ppl_poly_particle* rec_out, WsHeader* hdr, void* parts,
-                              ppl_is_result* res, cudaStream_t s);
+                              ppl_is_result* res, cudaStream_t s, const void* suff = nullptr);
+// Sufficient statistics of a data set for the line-fitting factor (one
+// block); `out` holds suffstat_bytes() bytes, 16-byte aligned.
+size_t suffstat_bytes();
+cudaError_t launch_suffstat(const float* x, const float* y, int64_t L, int d_max, void* out,
+                            cudaStream_t s);
 cudaError_t launch_stats(const float* lw, int64_t N, WsHeader* hdr, void* parts,
                          double* lse_out, cudaStream_t s);
 cudaError_t launch_posterior(const PolyParams& p, const ppl_poly_particle* rec, const float* lw,

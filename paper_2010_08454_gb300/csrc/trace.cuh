@@ -13,6 +13,7 @@
 #pragma once
 
 #include "posterior.cuh"
+#include "suffstat.cuh"
 
 namespace ppl {
 
@@ -211,7 +212,7 @@ __device__ __forceinline__ void trace_group(const Draw& draw, const PolyParams& 
                                             bool resident, float2* sdata, int64_t N,
                                             int64_t base, float* __restrict__ lw_out,
                                             ppl_poly_particle* __restrict__ rec_out,
-                                            TraceSmem<PPT>& ts) {
+                                            TraceSmem<PPT>& ts, const SuffStat* suff = nullptr) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
   // A. draw, write the records, rank every trace within its degree
@@ -292,7 +293,19 @@ __device__ __forceinline__ void trace_group(const Draw& draw, const PolyParams& 
     for (int k = 0; k < kMaxCoef; ++k)
       c[j][k] = (slot[j] < n_valid) ? ts.c[slot[j] * kCStride + k] : 0.0f;
   }
-  if (resident) {
+  if (suff != nullptr && suff->ok) {  // the same branch for the whole block
+    // sufficient statistics: O(d^2) per trace, d its own coefficient count
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      if (slot[j] < n_valid) {
+        int dk = 0;
+#pragma unroll
+        for (int k = 1; k < kMaxDegrees; ++k)
+          if (slot[j] >= ts.off[k]) dk = k;
+        ss[j] = suff_residual(*suff, c[j], p.min_deg + dk + p.coef_offset);
+      }
+    }
+  } else if (resident) {
     if (active) accumulate_dispatch<PPT>(nc, sdata, (int)L, c, ss, comp);
   } else {
     for (int64_t l0 = 0; l0 < L; l0 += chunk) {

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import gpu_is, load_ppl
+from gpu_util import check_is as _check, gpu_is, load_ppl
 
 pytestmark = pytest.mark.gpu
 
@@ -18,39 +18,6 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def ppl():
     return load_ppl()
-
-
-def _check(orc, res, lw, n, c, origin, x, y, N, seed, model_kw, full=True):
-    om = orc.poly_model(**model_kw)
-    ref, (lw_r, n_r, c_r) = orc.infer_is_poly(om, x, y, N, seed)
-    assert res["status"] == 0
-    assert np.array_equal(n, n_r)                                  # discrete draws: exact
-    assert np.array_equal(origin, np.arange(N))
-    assert np.allclose(c, c_r, rtol=1e-5, atol=1e-4)              # FP32 Box-Muller
-    err = np.abs(lw.astype(np.float64) - lw_r)
-    assert np.all(err <= 4e-6 * np.abs(lw_r) + 1e-3), float(np.max(err - 4e-6 * np.abs(lw_r)))
-    # 1e-3, widened by four FP32 ulps of the largest log-weight for data sets
-    # whose log-weights are so large that FP32 cannot resolve 1e-3
-    assert abs(res["log_z"] - ref["log_z"]) <= 1e-3 + 2.0 ** -21 * abs(ref["max_lw"])
-    assert res["ess"] == pytest.approx(ref["ess"], rel=1e-3)
-    assert res["max_lw"] == pytest.approx(ref["max_lw"], rel=4e-6, abs=1e-3)
-    if res["argmax"] != ref["argmax"]:  # a near-tie may order differently in FP32
-        assert abs(lw_r[res["argmax"]] - ref["max_lw"]) <= 4e-6 * abs(ref["max_lw"]) + 1e-3
-    assert np.allclose(res["p_n"], ref["p_n"], rtol=1e-4, atol=1e-12)
-    scale = np.max(np.abs(ref["mean_c"])) + 1e-12
-    assert np.allclose(res["mean_c"], ref["mean_c"], rtol=1e-4, atol=1e-5 * scale)
-    for d in range(ref["n_deg"]):
-        if ref["deg_argmax"][d] < 0:
-            continue
-        dm, dr = res["deg_mean"][d], ref["deg_mean"][d]
-        s = np.max(np.abs(dr)) + 1e-12
-        assert np.allclose(dm, dr, rtol=1e-4, atol=1e-5 * s), (d, dm, dr)
-        second = dr ** 2 + ref["deg_var"][d]
-        assert np.all(np.abs(res["deg_var"][d] - ref["deg_var"][d])
-                      <= 1e-3 * ref["deg_var"][d] + 1e-6 * second + 1e-9), d
-    assert res["map_deg"] == ref["map_deg"] or \
-        abs(ref["p_n"][res["map_deg"] - 2] - ref["p_n"][ref["map_deg"] - 2]) < 1e-6
-    return ref
 
 
 def test_linefitting_32_points_1e5_particles(ppl, orc):
