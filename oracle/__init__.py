@@ -99,6 +99,8 @@ def lib():
             "orc_enumerate": (ctypes.c_int, [ctypes.c_int, vp, i64, ctypes.c_int, vp, vp,
                                              ctypes.c_int]),
             "orc_is_discrete": (None, [ctypes.c_int, vp, i64, i64, u64, vp, vp]),
+            "orc_customdist_is": (None, [vp, vp, i64, i64, u64, vp, vp]),
+            "orc_customdist_exact": (None, [vp, vp, i64, vp]),
             "orc_set_threads": (None, [ctypes.c_int]),
             "orc_get_threads": (ctypes.c_int, []),
         }
@@ -329,3 +331,26 @@ def is_discrete(name, data, N, seed):
     vals, lw = np.zeros(N), np.zeros(N)
     lib().orc_is_discrete(DISCRETE_MODELS[name], _p(data), len(data), N, seed, _p(vals), _p(lw))
     return vals, lw
+
+
+# ---- customdist: a user-defined two-Gaussian density, observed --------------
+def customdist_params(w1=0.3, mu1=-2.0, s1=0.5, mu2=1.5, s2=1.0, obs_sigma=1.0):
+    """{w1, mu1, s1, mu2, s2, obs_sigma} as FP64 (the GPU takes the same values as FP32)."""
+    return np.array([w1, mu1, s1, mu2, s2, obs_sigma], dtype=np.float32).astype(np.float64)
+
+
+def customdist_is(prm, y, N, seed):
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    x, lw = np.zeros(N), np.zeros(N)
+    lib().orc_customdist_is(_p(np.ascontiguousarray(prm, dtype=np.float64)), _p(y), len(y), N,
+                            seed, _p(x), _p(lw))
+    return x, lw
+
+
+def customdist_exact(prm, y):
+    """log Z, posterior mean and variance of x (closed form)."""
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    out = np.zeros(3)
+    lib().orc_customdist_exact(_p(np.ascontiguousarray(prm, dtype=np.float64)), _p(y), len(y),
+                               _p(out))
+    return {"log_z": out[0], "mean": out[1], "var": out[2]}

@@ -10,7 +10,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SOURCES = ["philox.c", "poly.c", "normalize.c", "resample.c", "lgssm.c", "conjugate.c",
-           "enumerate.c", "mlp.c"]
+           "enumerate.c", "mlp.c", "customdist.c"]
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liboracle.so")
 

@@ -106,6 +106,10 @@ double orc_poly_exact(const orc_poly* m, const double* x, const double* y, int64
 /* ---- exact enumeration of tiny discrete models (enumerate.c) ---------- */
 int orc_enumerate(int model, const int32_t* data, int64_t n_data, int max_depth,
                   double* values, double* probs, int max_out);
+/* customdist (customdist.c): prm = {w1, mu1, s1, mu2, s2, obs_sigma}. */
+void orc_customdist_is(const double* prm, const float* y, int64_t n, int64_t N, uint64_t seed,
+                       double* x_out, double* lw_out);
+void orc_customdist_exact(const double* prm, const float* y, int64_t n, double* out);
 void orc_is_discrete(int model, const int32_t* data, int64_t n_data, int64_t N, uint64_t seed,
                      double* values, double* lw);
 
