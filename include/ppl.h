@@ -101,6 +101,43 @@ typedef struct {
   int32_t status, pad;
 } ppl_is_result;
 
+/* The paper's tiny discrete benchmarks (Table 1 of §5.1). */
+typedef enum {
+  PPL_DISCRETE_BIASEDCOIN = 0, /* theta = a/10, a ~ uniform-discrete(1,9); observe flips */
+  PPL_DISCRETE_BINOMIAL = 1,   /* successes among `limit` bernoulli(0.3) samples */
+  PPL_DISCRETE_GEOMETRIC = 2   /* bernoulli(0.5) failures before a success, < `limit` */
+} ppl_discrete_model;
+
+#define PPL_DISCRETE_MAX_VALUES 64
+
+/* The normalised distribution of a discrete model's return value.  Value code
+ * v: biasedcoin theta = (v + 1)/10 (9 codes); binomial k = v (limit + 1
+ * codes); geometric c = v (limit + 1 codes, the last one -- the limit reached
+ * -- outside the truncated support).  [dev] like ppl_is_result. */
+typedef struct {
+  double log_z, ess, max_lw;
+  double mean;  /* sum over codes of prob * value */
+  int64_t n_particles;
+  int32_t n_values, status;
+  double value[PPL_DISCRETE_MAX_VALUES];
+  double prob[PPL_DISCRETE_MAX_VALUES];
+  int64_t count[PPL_DISCRETE_MAX_VALUES]; /* particles that returned each code */
+} ppl_discrete_result;
+
+/* The customdist benchmark (Table 1 of §5.1): a user-defined distribution
+ * whose density is w1 N(mu1, sigma1^2) + (1 - w1) N(mu2, sigma2^2), its draw
+ * observed through normal(x, obs_sigma) at every data point. */
+typedef struct {
+  float w1, mu1, sigma1, mu2, sigma2, obs_sigma;
+} ppl_customdist_model;
+
+typedef struct {
+  double log_z, lse, ess, max_lw;
+  double mean_x, var_x; /* posterior mean and variance of x under the normalised weights */
+  int64_t n_particles;
+  int32_t status, pad;
+} ppl_customdist_result;
+
 /* Readable name of a status code.  Never NULL. */
 const char* ppl_status_string(int32_t status);
 
@@ -149,6 +186,32 @@ ppl_status ppl_infer_is_suffstat(const ppl_model* model, const ppl_data* data,
                                  ppl_is_result* out_dev, float* lw_out,
                                  ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,
                                  ppl_stream stream);
+
+/* Likelihood weighting (§3.6.2) on a tiny discrete benchmark (Table 1 of
+ * §5.1).  Each `sample` takes one Philox word, in program order, from blocks
+ * 0, 1, ... of counter (particle, 0, 0, POLY_TRACE); bernoulli(p) is
+ * u01(w) < p, decided exactly on the word's top 23 bits.  flips [dev, int32,
+ * 0/1, n_flips] are biasedcoin's observations; `limit` is binomial's number
+ * of trials (0..63) or geometric's depth (1..63).  Writes *out_dev; codes_out
+ * and lw_out [dev, n_particles] are optional per-particle outputs.  `ws` needs
+ * ppl_workspace_size(model, 1, 0) bytes for any model.  Invalid model, limit
+ * or n_particles -> PPL_EINVAL; no finite weight -> PPL_EEMPTY in the status. */
+ppl_status ppl_infer_discrete(int32_t model, const int32_t* flips, int64_t n_flips, int32_t limit,
+                              int64_t n_particles, uint64_t seed, ppl_discrete_result* out_dev,
+                              int32_t* codes_out, float* lw_out, void* ws, size_t ws_bytes,
+                              ppl_stream stream);
+
+/* Likelihood weighting (§3.6.2) on customdist: x from the user-defined
+ * density (component 1 when u01(w0) < w1, then mu + sigma z with z the first
+ * Box-Muller normal of words 1, 2; block 0 of counter (particle, 0, 0,
+ * POLY_TRACE)); lw = sum_j log N(y_j; x, obs_sigma^2).  y [dev, FP32, n_obs];
+ * writes *out_dev; x_out and lw_out [dev, n_particles] optional.  `ws` needs
+ * ppl_workspace_size(model, n_particles, 0) bytes for any ppl_model.  Invalid
+ * weights (w1 outside [0, 1]) or scales (not positive) -> PPL_EINVAL. */
+ppl_status ppl_infer_customdist(const ppl_customdist_model* model, const float* y, int64_t n_obs,
+                                int64_t n_particles, uint64_t seed,
+                                ppl_customdist_result* out_dev, float* x_out, float* lw_out,
+                                void* ws, size_t ws_bytes, ppl_stream stream);
 
 /* Same as ppl_infer_is with the data and the result in host memory: copies x,
  * y in, runs, copies the summary out, and synchronises `stream` before it

@@ -62,6 +62,44 @@ class PplIsResult(ctypes.Structure):
 
 RESULT_BYTES = ctypes.sizeof(PplIsResult)
 
+class PplCustomdistModel(ctypes.Structure):
+    _fields_ = [("w1", ctypes.c_float), ("mu1", ctypes.c_float), ("sigma1", ctypes.c_float),
+                ("mu2", ctypes.c_float), ("sigma2", ctypes.c_float), ("obs_sigma", ctypes.c_float)]
+
+
+class PplCustomdistResult(ctypes.Structure):
+    _fields_ = [("log_z", ctypes.c_double), ("lse", ctypes.c_double), ("ess", ctypes.c_double),
+                ("max_lw", ctypes.c_double), ("mean_x", ctypes.c_double),
+                ("var_x", ctypes.c_double), ("n_particles", ctypes.c_int64),
+                ("status", ctypes.c_int32), ("pad", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+def customdist_model(w1=0.3, mu1=-2.0, sigma1=0.5, mu2=1.5, sigma2=1.0, obs_sigma=1.0):
+    return PplCustomdistModel(w1, mu1, sigma1, mu2, sigma2, obs_sigma)
+
+
+PPL_DISCRETE_MAX_VALUES = 64
+DISCRETE_MODELS = {"biasedcoin": 0, "binomial": 1, "geometric": 2}
+
+
+class PplDiscreteResult(ctypes.Structure):
+    _fields_ = [("log_z", ctypes.c_double), ("ess", ctypes.c_double),
+                ("max_lw", ctypes.c_double), ("mean", ctypes.c_double),
+                ("n_particles", ctypes.c_int64), ("n_values", ctypes.c_int32),
+                ("status", ctypes.c_int32), ("value", ctypes.c_double * PPL_DISCRETE_MAX_VALUES),
+                ("prob", ctypes.c_double * PPL_DISCRETE_MAX_VALUES),
+                ("count", ctypes.c_int64 * PPL_DISCRETE_MAX_VALUES)]
+
+    def as_dict(self):
+        n = self.n_values
+        return {"log_z": self.log_z, "ess": self.ess, "max_lw": self.max_lw, "mean": self.mean,
+                "n_particles": self.n_particles, "n_values": n, "status": self.status,
+                "value": np.array(self.value[:n]), "prob": np.array(self.prob[:n]),
+                "count": np.array(self.count[:n])}
+
 
 class PplBatchPlan(ctypes.Structure):
     _fields_ = [("ppt", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
@@ -85,6 +123,14 @@ _SIGS = {
                                              ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_size_t, ctypes.c_void_p]),
+    "ppl_infer_customdist": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                            ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_size_t, ctypes.c_void_p]),
+    "ppl_infer_discrete": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int64,
+                                          ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
     "ppl_infer_is_host": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                          ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
@@ -296,6 +342,39 @@ def ppl_infer_is_suffstat(model, x, y, n_particles, seed, instance=0, out=None, 
                                      _stream(stream))
     _check(st, "ppl_infer_is_suffstat")
     return out
+
+
+def ppl_infer_customdist(model, y, n_particles, seed, x_out=None, lw_out=None, ws=None,
+                         stream=None):
+    """Likelihood weighting on customdist; returns the decoded result."""
+    if y is not None and y.numel() > 0:
+        _dev_f32(y, "y")
+    if ws is None:
+        ws = workspace(poly_model(), n_particles, 0)
+    out = torch.zeros(ctypes.sizeof(PplCustomdistResult), dtype=torch.uint8, device=ws.device)
+    n = 0 if y is None else y.numel()
+    st = lib().ppl_infer_customdist(ctypes.byref(model), _ptr(y) if n else None, n,
+                                    int(n_particles), ctypes.c_uint64(seed), _ptr(out),
+                                    _ptr(x_out), _ptr(lw_out), _ptr(ws), ws.numel(),
+                                    _stream(stream))
+    _check(st, "ppl_infer_customdist")
+    return PplCustomdistResult.from_buffer_copy(out.cpu().numpy().tobytes()).as_dict()
+
+
+def ppl_infer_discrete(model, n_particles, seed, flips=None, limit=0, codes_out=None,
+                       lw_out=None, ws=None, stream=None):
+    """Likelihood weighting on a tiny discrete benchmark; returns the decoded result."""
+    m = DISCRETE_MODELS[model] if isinstance(model, str) else int(model)
+    if ws is None:
+        ws = workspace(poly_model(), 1, 0)
+    out = torch.zeros(ctypes.sizeof(PplDiscreteResult), dtype=torch.uint8, device=ws.device)
+    n_flips = 0 if flips is None else flips.numel()
+    st = lib().ppl_infer_discrete(m, _ptr(flips), n_flips, int(limit), int(n_particles),
+                                  ctypes.c_uint64(seed), _ptr(out), _ptr(codes_out), _ptr(lw_out),
+                                  _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "ppl_infer_discrete")
+    raw = out.cpu().numpy().tobytes()
+    return PplDiscreteResult.from_buffer_copy(raw).as_dict()
 
 
 def ppl_infer_is_host(model, x_host, y_host, n_particles, seed, ws, stream=None):

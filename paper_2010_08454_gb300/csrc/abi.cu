@@ -174,6 +174,60 @@ ppl_status ppl_infer_is_suffstat(const ppl_model* model, const ppl_data* data,
   return PPL_OK;
 }
 
+ppl_status ppl_infer_discrete(int32_t model, const int32_t* flips, int64_t n_flips, int32_t limit,
+                              int64_t n_particles, uint64_t seed, ppl_discrete_result* out_dev,
+                              int32_t* codes_out, float* lw_out, void* ws, size_t ws_bytes,
+                              ppl_stream stream) {
+  if (!out_dev || n_particles < 1 || n_particles > kMaxParticles) return PPL_EINVAL;
+  int32_t n_values = 0;
+  double p = 0.0;
+  if (model == PPL_DISCRETE_BIASEDCOIN) {
+    if (n_flips < 0 || n_flips > 0x7fffffff || (n_flips > 0 && !flips)) return PPL_EINVAL;
+    n_values = 9;
+  } else if (model == PPL_DISCRETE_BINOMIAL) {
+    if (limit < 0 || limit >= PPL_DISCRETE_MAX_VALUES) return PPL_EINVAL;
+    n_values = limit + 1;
+    p = 0.3;
+  } else if (model == PPL_DISCRETE_GEOMETRIC) {
+    if (limit < 1 || limit >= PPL_DISCRETE_MAX_VALUES) return PPL_EINVAL;
+    n_values = limit + 1;
+    p = 0.5;
+  } else {
+    return PPL_EINVAL;
+  }
+  // u01(w) = ((w >> 9) + 0.5) 2^-23 < p  <=>  (w >> 9) < ceil(p 2^23 - 0.5), exact in FP64
+  const uint32_t threshold = (uint32_t)ceil(p * 8388608.0 - 0.5);
+  Ws w;
+  PPL_TRY(check_ws(ws, ws_bytes, 1, 0, &w));
+  cudaStream_t s = (cudaStream_t)stream;
+  PPL_TRY(reset_ws(w, false, s));
+  PPL_TRY(cuda_status(launch_discrete_is(model, flips, model == PPL_DISCRETE_BIASEDCOIN ? n_flips : 0,
+                                         limit, n_particles, seed, threshold, n_values, codes_out,
+                                         lw_out, w.partials(), w.hdr(), out_dev, s)));
+  return PPL_OK;
+}
+
+ppl_status ppl_infer_customdist(const ppl_customdist_model* model, const float* y, int64_t n_obs,
+                                int64_t n_particles, uint64_t seed,
+                                ppl_customdist_result* out_dev, float* x_out, float* lw_out,
+                                void* ws, size_t ws_bytes, ppl_stream stream) {
+  if (!model || !out_dev || n_particles < 1 || n_particles > kMaxParticles) return PPL_EINVAL;
+  if (n_obs < 0 || (n_obs > 0 && !y)) return PPL_EINVAL;
+  if (!(model->w1 >= 0.0f && model->w1 <= 1.0f) || !(model->sigma1 > 0.0f) ||
+      !(model->sigma2 > 0.0f) || !(model->obs_sigma > 0.0f) || !isfinite(model->mu1) ||
+      !isfinite(model->mu2))
+    return PPL_EINVAL;
+  // u01(w) = ((w >> 9) + 0.5) 2^-23 < w1  <=>  (w >> 9) < ceil(w1 2^23 - 0.5), exact in FP64
+  const uint32_t threshold = (uint32_t)std::max(0.0, ceil((double)model->w1 * 8388608.0 - 0.5));
+  Ws w;
+  PPL_TRY(check_ws(ws, ws_bytes, n_particles, 0, &w));
+  cudaStream_t s = (cudaStream_t)stream;
+  PPL_TRY(reset_ws(w, false, s));
+  PPL_TRY(cuda_status(launch_customdist(*model, threshold, y, n_obs, n_particles, seed, x_out,
+                                        lw_out, w.partials(), w.hdr(), out_dev, s)));
+  return PPL_OK;
+}
+
 ppl_status ppl_infer_is(const ppl_model* model, const ppl_data* data, int64_t n_particles,
                         uint64_t seed, ppl_is_result* out_dev, float* lw_out,
                         ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,

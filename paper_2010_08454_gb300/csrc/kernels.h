@@ -25,6 +25,14 @@ cudaError_t launch_poly_trace(const PolyParams& p, const float* x, const float* 
 // Sufficient statistics of a data set for the line-fitting factor (one
 // block); `out` holds suffstat_bytes() bytes, 16-byte aligned.
 size_t suffstat_bytes();
+cudaError_t launch_customdist(const ppl_customdist_model& m, uint32_t comp_threshold,
+                              const float* y, int64_t n, int64_t N, uint64_t seed, float* x_out,
+                              float* lw_out, void* parts, WsHeader* hdr,
+                              ppl_customdist_result* res, cudaStream_t s);
+cudaError_t launch_discrete_is(int32_t model, const int32_t* data, int64_t n_data, int32_t limit,
+                               int64_t N, uint64_t seed, uint32_t bern_threshold, int32_t n_values,
+                               int32_t* codes_out, float* lw_out, void* counts, WsHeader* hdr,
+                               ppl_discrete_result* res, cudaStream_t s);
 cudaError_t launch_suffstat(const float* x, const float* y, int64_t L, int d_max, void* out,
                             cudaStream_t s);
 cudaError_t launch_stats(const float* lw, int64_t N, WsHeader* hdr, void* parts,

@@ -66,6 +66,19 @@ def test_host_side_argument_checks(ppl):
                             None, None, ctypes.c_void_p(264), 1 << 30, None) == ppl.PPL_EINVAL
     assert lib.ppl_infer_is(ctypes.byref(m), ctypes.byref(data), 10, 0, ctypes.c_void_p(256),
                             None, None, ctypes.c_void_p(256), 100, None) == ppl.PPL_EINVAL
+    # discrete benchmarks: unknown model, limit out of range, null result
+    for model, limit in [(7, 3), (1, 64), (1, -1), (2, 0), (2, 64)]:
+        assert lib.ppl_infer_discrete(model, None, 0, limit, 10, 0, ctypes.c_void_p(256), None,
+                                      None, ctypes.c_void_p(256), 1 << 30,
+                                      None) == ppl.PPL_EINVAL
+    assert lib.ppl_infer_discrete(1, None, 0, 3, 10, 0, None, None, None, ctypes.c_void_p(256),
+                                  1 << 30, None) == ppl.PPL_EINVAL
+    # customdist: invalid weight or scale
+    for kw in [dict(w1=1.5), dict(sigma1=0.0), dict(obs_sigma=-1.0)]:
+        cm = ppl.customdist_model(**kw)
+        assert lib.ppl_infer_customdist(ctypes.byref(cm), None, 0, 10, 0, ctypes.c_void_p(256),
+                                        None, None, ctypes.c_void_p(256), 1 << 30,
+                                        None) == ppl.PPL_EINVAL
     # resample needs exactly one of lw / q_fixed
     assert lib.ppl_resample(None, None, 10, 10, 0, 0, 0, ctypes.c_void_p(256),
                             ctypes.c_void_p(256), 1 << 30, None) == ppl.PPL_EINVAL
