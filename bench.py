@@ -58,7 +58,7 @@ def parse():
                     help="skip the state-space, batched and learned-proposal workloads")
     ap.add_argument("--particles", type=int, default=N_PARTICLES,
                     help="particles per step (smaller cases for profiling only)")
-    ap.add_argument("--config", choices=["smc", "batched", "learned", "suffstat"],
+    ap.add_argument("--config", choices=["smc", "batched", "learned", "suffstat", "small"],
                     help="run only this secondary workload and print its line (profiling)")
     return ap.parse_args()
 
@@ -283,6 +283,35 @@ def bench_suffstat(torch, ppl, reps=10):
             "unit": "traces/s", "ms_per_launch": times["suffstat"],
             "direct_ms_per_launch": times["direct"], "log_z": summary["log_z"],
             "gpu_launches_per_call": 2}
+
+
+def bench_small_models(torch, ppl, reps=10):
+    """The paper's other importance-sampling benchmarks (Table 1): biasedcoin,
+    binomial, a truncated geometric and customdist, 2^24 particles each."""
+    import numpy as np
+    N = 1 << 24
+    rng = np.random.default_rng(12)
+    flips = torch.tensor((rng.random(200) < 0.7).astype(np.int32), device="cuda")
+    y = torch.tensor(rng.normal(1.0, 1.0, 8).astype(np.float32), device="cuda")
+    ws = ppl.workspace(ppl.poly_model(), N, 0)
+    cm = ppl.customdist_model()
+    runs = {
+        "biasedcoin_200_flips": lambda: ppl.ppl_infer_discrete("biasedcoin", N, 1, flips=flips, ws=ws),
+        "binomial_10_trials": lambda: ppl.ppl_infer_discrete("binomial", N, 1, limit=10, ws=ws),
+        "geometric_depth_12": lambda: ppl.ppl_infer_discrete("geometric", N, 1, limit=12, ws=ws),
+        "customdist_8_obs": lambda: ppl.ppl_infer_customdist(cm, y, N, 1, ws=ws),
+    }
+    out = {}
+    for name, fn in runs.items():
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        ms = float(np.median([_event_ms(torch, fn, 1) for _ in range(reps)]))
+        out[name] = {"ms_per_call": ms, "traces_per_s": N / (ms / 1e3)}
+    return {"workload": "likelihood weighting, 2^24 particles per model; each call includes its "
+                        "result's device-to-host copy (the binding decodes it)",
+            "metric": "particle-traces/sec", "unit": "traces/s", "models": out,
+            "gpu_launches_per_call": 1}
 
 
 def bench_batched(torch, ppl, reps=5):
@@ -575,6 +604,7 @@ def run_ours(args):
     if not args.no_configs:
         out["configs"] = {"smc_lgssm_T200_2e20": bench_smc(torch, ppl),
                           "suffstat_linefitting_2e24x256": bench_suffstat(torch, ppl),
+                          "small_models_2e24": bench_small_models(torch, ppl),
                           "batched_4096": bench_batched(torch, ppl),
                           "learned_proposal_1024x2e20": bench_learned(torch, ppl)}
     if not args.no_cpu_baseline:
@@ -590,7 +620,7 @@ def run_config(args):
     torch.cuda.set_device(0)
     ppl.lib()
     fn = {"smc": bench_smc, "batched": bench_batched, "learned": bench_learned,
-          "suffstat": bench_suffstat}[args.config]
+          "suffstat": bench_suffstat, "small": bench_small_models}[args.config]
     print(json.dumps({"config": args.config, "result": fn(torch, ppl)}), flush=True)
     return 0
 
