@@ -70,6 +70,23 @@ def dist_env():
     return rank, world, local
 
 
+def reduce_max(values, world, device=None):
+    """The maximum over ranks of each value; every rank gets the result (one
+    all-reduce of a few doubles, host timing only -- no data-path exchange)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def weak_scaling_value(world, units_per_rank, steps, max_ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank * steps / (max_ms / 1e3)
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -539,12 +556,8 @@ def run_ours(args):
 
     stage = np.array([[ev[i].elapsed_time(ev[i + 1]) for i in range(4)] for ev in events])
     step_ms = stage.sum(axis=1)
-    total_ms = float(step_ms.sum())
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * N * args.steps / (total_ms / 1e3)
+    (total_ms,) = reduce_max([float(step_ms.sum())], world, dev)
+    value = weak_scaling_value(world, N, args.steps, total_ms)
 
     # end to end through the public API with host buffers: pinned H2D of the data,
     # the whole step, D2H of the posterior summary
@@ -563,8 +576,8 @@ def run_ours(args):
         ppl.ppl_gather(parts, anc, state_out=parts_out)
         res_h.copy_(res, non_blocking=True)
         torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    e2e_value = world * N * n_e2e / e2e_s if n_e2e else None  # every rank runs the same loop
+    (e2e_s,) = reduce_max([time.perf_counter() - t0], world, dev)
+    e2e_value = weak_scaling_value(world, N, n_e2e, e2e_s * 1e3) if n_e2e else None
 
     if world > 1:
         torch.distributed.destroy_process_group()
