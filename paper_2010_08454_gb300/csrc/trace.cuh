@@ -236,29 +236,35 @@ __device__ __forceinline__ void trace_group(const Draw& draw, const PolyParams& 
     }
   }
   __syncthreads();
-  // exclusive offsets in (degree, q, warp) order: deterministic sorted order
-  if (tid < kMaxDegrees) {
-    int tot = 0;
-    for (int q = 0; q < PPT; ++q)
-      for (int w = 0; w < kTpb / 32; ++w) tot += ts.wcount[q][w][tid];
-    ts.off[tid + 1] = tot;
-  }
-  if (tid == 0) ts.nan = 0;
-  __syncthreads();
-  if (tid == 0) {
-    ts.off[0] = 0;
-    for (int k = 0; k < kMaxDegrees; ++k) ts.off[k + 1] += ts.off[k];
-  }
-  __syncthreads();
-  for (int e = tid; e < kMaxDegrees * PPT * (kTpb / 32); e += kTpb) {
-    // running offset of (q, warp) within degree k, in (q, warp) order
-    const int k = e % kMaxDegrees, qw = e / kMaxDegrees;
-    const int q = qw / (kTpb / 32), w = qw % (kTpb / 32);
-    int before = ts.off[k];
-    for (int qq = 0; qq < PPT; ++qq)
-      for (int ww = 0; ww < kTpb / 32; ++ww)
-        if (qq * (kTpb / 32) + ww < qw) before += ts.wcount[qq][ww][k];
-    ts.wbase[q][w][k] = before;
+  // exclusive offsets in (degree, q, warp) order: deterministic sorted order.
+  // One warp scans the 4 PPT 8 counts in that order; the scan at the first
+  // entry of degree k is off[k], and every entry's scan is its wbase.
+  if (warp == 0) {
+    constexpr int W = kTpb / 32, E = kMaxDegrees * PPT * W, R = E / 32;
+    static_assert(E % 32 == 0 && (PPT * W) % R == 0, "whole entries per lane");
+    int v[R];
+    int run = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int f = lane * R + r, k = f / (PPT * W), qw = f % (PPT * W);
+      v[r] = run;
+      run += ts.wcount[qw / W][qw % W][k];
+    }
+    int inc = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += y;
+    }
+    const int ex = inc - run;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int f = lane * R + r, k = f / (PPT * W), qw = f % (PPT * W);
+      ts.wbase[qw / W][qw % W][k] = ex + v[r];
+      if (qw == 0) ts.off[k] = ex + v[r];
+    }
+    if (lane == 31) ts.off[kMaxDegrees] = inc;
+    if (lane == 0) ts.nan = 0;
   }
   __syncthreads();
 #pragma unroll
