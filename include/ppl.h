@@ -213,6 +213,17 @@ ppl_status ppl_infer_customdist(const ppl_customdist_model* model, const float* 
                                 ppl_customdist_result* out_dev, float* x_out, float* lw_out,
                                 void* ws, size_t ws_bytes, ppl_stream stream);
 
+/* The proposal network's matrix product on the fifth-generation tensor
+ * cores: C[m, n] = sum_k A(m, k) B(n, k), A(m, k) = A[m sam + k sak],
+ * B(n, k) = B[n sbn + k sbk] (BF16, any strides: transposed operands are read
+ * in place), C [dev, FP32, M x N row-major], FP32 accumulation.  A wait that
+ * runs out is reported through ppl_workspace_status(ws); `ws` needs
+ * ppl_workspace_size(model, 1, 0) bytes for any model.  M, N, K >= 1 and
+ * below 2^24 (else PPL_EINVAL). */
+ppl_status ppl_gemm_bf16(const void* A, int64_t sam, int64_t sak, const void* B, int64_t sbn,
+                         int64_t sbk, int32_t M, int32_t N, int32_t K, float* C, void* ws,
+                         size_t ws_bytes, ppl_stream stream);
+
 /* Same as ppl_infer_is with the data and the result in host memory: copies x,
  * y in, runs, copies the summary out, and synchronises `stream` before it
  * returns.  The workspace must also hold the data (see ppl_workspace_size). */
@@ -355,7 +366,9 @@ ppl_status ppl_batched_status(const void* ws, ppl_stream stream);
  * posterior (§3.6.2).  Network: in[64] = the points sorted by x, (x, y/10),
  * BF16; h1 = relu(W1 in + b1), h2 = relu(W2 h1 + b2) with 256 units, out =
  * W3 h2 + b3 with 48 outputs; BF16 weights and activations on the tensor
- * cores, FP32 accumulation, FP32 biases.  out[0..n_deg) are degree logits;
+ * cores (tcgen05, accumulator in tensor memory; ppl_gemm_bf16), FP32
+ * accumulation, FP32 biases.  A tensor-core wait that runs out sets the first
+ * word of the proposal workspace (read it with ppl_workspace_status).  out[0..n_deg) are degree logits;
  * coefficient j of degree slot k (slots in order, ncoef_k = min_deg + k +
  * coef_offset) has mu = prior_sigma out[4 + 2 i], s = prior_sigma exp(clamp(
  * out[5 + 2 i], -9, 1)), i = ncoef_0 + .. + ncoef_{k-1} + j.

@@ -123,6 +123,11 @@ _SIGS = {
                                              ctypes.c_uint64, ctypes.c_uint32, ctypes.c_void_p,
                                              ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                              ctypes.c_size_t, ctypes.c_void_p]),
+    "ppl_gemm_bf16": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                     ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                     ctypes.c_void_p]),
     "ppl_infer_customdist": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
                                             ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -342,6 +347,20 @@ def ppl_infer_is_suffstat(model, x, y, n_particles, seed, instance=0, out=None, 
                                      _stream(stream))
     _check(st, "ppl_infer_is_suffstat")
     return out
+
+
+def ppl_gemm_bf16(A, B, M, N, K, sam, sak, sbn, sbk, C=None, ws=None, stream=None):
+    """C[m, n] = sum_k A[m sam + k sak] B[n sbn + k sbk] on the tensor cores (BF16 in, FP32 out)."""
+    if A.dtype != torch.bfloat16 or B.dtype != torch.bfloat16:
+        raise TypeError("A and B must be bfloat16")
+    if ws is None:
+        ws = workspace(poly_model(), 1, 0)
+    if C is None:
+        C = torch.empty((M, N), dtype=torch.float32, device=A.device)
+    st = lib().ppl_gemm_bf16(_ptr(A), sam, sak, _ptr(B), sbn, sbk, M, N, K, _ptr(C), _ptr(ws),
+                             ws.numel(), _stream(stream))
+    _check(st, "ppl_gemm_bf16")
+    return C, ws
 
 
 def ppl_infer_customdist(model, y, n_particles, seed, x_out=None, lw_out=None, ws=None,

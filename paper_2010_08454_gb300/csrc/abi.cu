@@ -228,6 +228,21 @@ ppl_status ppl_infer_customdist(const ppl_customdist_model* model, const float* 
   return PPL_OK;
 }
 
+ppl_status ppl_gemm_bf16(const void* A, int64_t sam, int64_t sak, const void* B, int64_t sbn,
+                         int64_t sbk, int32_t M, int32_t N, int32_t K, float* C, void* ws,
+                         size_t ws_bytes, ppl_stream stream) {
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || M >= (1 << 24) || N >= (1 << 24) ||
+      K >= (1 << 24))
+    return PPL_EINVAL;
+  Ws w;
+  PPL_TRY(check_ws(ws, ws_bytes, 1, 0, &w));
+  cudaStream_t s = (cudaStream_t)stream;
+  PPL_TRY(reset_ws(w, false, s));
+  return cuda_status(launch_umma_gemm(reinterpret_cast<const __nv_bfloat16*>(A), sam, sak,
+                                      reinterpret_cast<const __nv_bfloat16*>(B), sbn, sbk, M, N,
+                                      K, nullptr, nullptr, 0, C, nullptr, &w.hdr()->status, s));
+}
+
 ppl_status ppl_infer_is(const ppl_model* model, const ppl_data* data, int64_t n_particles,
                         uint64_t seed, ppl_is_result* out_dev, float* lw_out,
                         ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,

@@ -1,6 +1,8 @@
 // Internal launch interface between the C ABI (abi.cu) and the kernels.
 #pragma once
 
+#include <cuda_bf16.h>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -25,6 +27,10 @@ cudaError_t launch_poly_trace(const PolyParams& p, const float* x, const float* 
 // Sufficient statistics of a data set for the line-fitting factor (one
 // block); `out` holds suffstat_bytes() bytes, 16-byte aligned.
 size_t suffstat_bytes();
+cudaError_t launch_umma_gemm(const __nv_bfloat16* A, int64_t sam, int64_t sak,
+                             const __nv_bfloat16* B, int64_t sbn, int64_t sbk, int M, int N, int K,
+                             const float* bias, const __nv_bfloat16* mask, int relu, float* Cf,
+                             __nv_bfloat16* Cb, int32_t* status, cudaStream_t s);
 cudaError_t launch_customdist(const ppl_customdist_model& m, uint32_t comp_threshold,
                               const float* y, int64_t n, int64_t N, uint64_t seed, float* x_out,
                               float* lw_out, void* parts, WsHeader* hdr,

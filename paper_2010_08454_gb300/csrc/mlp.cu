@@ -99,14 +99,11 @@ __global__ void __launch_bounds__(kTpb) forward_sim_kernel(PolyParams p, float o
 }
 
 // ---------------------------------------------------------------------------
-// BF16 GEMM on the tensor cores (mma.sync m16n8k16, FP32 accumulation):
+// BF16 GEMM on the fifth-generation tensor cores (umma_gemm.cu):
 //   C[m, n] = sum_k A(m, k) B(n, k)  (+ bias[n]) (relu) (* [mask(m, n) > 0])
 // A(m, k) = A[m * sam + k * sak], B(n, k) = B[n * sbn + k * sbk]: any layout,
-// so the backward products read transposed operands in place.  Block tile
-// 64 x 64 x 32, four warps of 32 x 32.
+// so the backward products read transposed operands in place.
 // ---------------------------------------------------------------------------
-constexpr int kGM = 64, kGN = 64, kGK = 32, kGPad = 8;
-
 struct GemmArgs {
   const __nv_bfloat16* A;
   int64_t sam, sak;
@@ -120,85 +117,9 @@ struct GemmArgs {
   __nv_bfloat16* Cb;   // BF16 output [M x N], optional
 };
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const uint32_t (&a)[4],
-                                         const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-__global__ void __launch_bounds__(128) gemm_bf16_kernel(GemmArgs g) {
-  __shared__ __align__(16) __nv_bfloat16 As[kGM][kGK + kGPad];
-  __shared__ __align__(16) __nv_bfloat16 Bs[kGN][kGK + kGPad];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int m0 = blockIdx.y * kGM, n0 = blockIdx.x * kGN;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int gid = lane >> 2, tig = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) acc[i][j][r] = 0.0f;
-  const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
-  for (int k0 = 0; k0 < g.K; k0 += kGK) {
-    for (int e = tid; e < kGM * kGK; e += 128) {
-      const int r = e / kGK, k = e % kGK;
-      const int gm = m0 + r, gk = k0 + k;
-      As[r][k] = (gm < g.M && gk < g.K) ? g.A[gm * g.sam + gk * g.sak] : zero;
-      const int gn = n0 + r;
-      Bs[r][k] = (gn < g.N && gk < g.K) ? g.B[gn * g.sbn + gk * g.sbk] : zero;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < kGK; kk += 16) {
-      uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i) {
-        const int r = wm + i * 16 + gid;
-        af[i][0] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 2 * tig]);
-        af[i][1] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 2 * tig]);
-        af[i][2] = *reinterpret_cast<const uint32_t*>(&As[r][kk + 8 + 2 * tig]);
-        af[i][3] = *reinterpret_cast<const uint32_t*>(&As[r + 8][kk + 8 + 2 * tig]);
-      }
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        const int c = wn + j * 8 + gid;
-        bfr[j][0] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + 2 * tig]);
-        bfr[j][1] = *reinterpret_cast<const uint32_t*>(&Bs[c][kk + 8 + 2 * tig]);
-      }
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int m = m0 + wm + i * 16 + gid + (r >= 2 ? 8 : 0);
-        const int n = n0 + wn + j * 8 + 2 * tig + (r & 1);
-        if (m >= g.M || n >= g.N) continue;
-        float v = acc[i][j][r];
-        if (g.bias) v += g.bias[n];
-        if (g.relu) v = fmaxf(v, 0.0f);
-        if (g.mask && !(__bfloat162float(g.mask[(int64_t)m * g.N + n]) > 0.0f)) v = 0.0f;
-        if (g.Cf) g.Cf[(int64_t)m * g.N + n] = v;
-        if (g.Cb) g.Cb[(int64_t)m * g.N + n] = __float2bfloat16_rn(v);
-      }
-}
-
-static cudaError_t gemm(const GemmArgs& g, cudaStream_t s) {
-  dim3 grid((g.N + kGN - 1) / kGN, (g.M + kGM - 1) / kGM);
-  gemm_bf16_kernel<<<grid, 128, 0, s>>>(g);
-  return cudaGetLastError();
+static cudaError_t gemm(const GemmArgs& g, int32_t* status, cudaStream_t s) {
+  return launch_umma_gemm(g.A, g.sam, g.sak, g.B, g.sbn, g.sbk, g.M, g.N, g.K, g.bias, g.mask,
+                          g.relu, g.Cf, g.Cb, status, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -312,6 +233,7 @@ __global__ void bump_kernel(int32_t* step) { *step += 1; }
 // Workspace of the network for a batch of B rows.
 // ---------------------------------------------------------------------------
 struct MlpWs {
+  int32_t* status;  // first word: a tensor-core wait that ran out (ppl_workspace_status)
   __nv_bfloat16 *pb, *feat, *h1, *h2, *dout_b, *dh2, *dh1;
   float *out, *dout, *grad;
   int32_t* n_t;
@@ -331,6 +253,7 @@ static MlpWs mlp_ws(char* base, int64_t B) {
     off += a256(bytes);
     return p;
   };
+  w.status = (int32_t*)take(sizeof(int32_t));
   w.step = (int32_t*)take(sizeof(int32_t));
   w.loss = (double*)take(sizeof(double) * 2);
   w.pb = (__nv_bfloat16*)take(kNumParams * 2);
@@ -354,18 +277,18 @@ static cudaError_t mlp_forward(const float* params, const MlpWs& w, int B, cudaS
   g.A = w.feat; g.sam = kIn; g.sak = 1;
   g.B = w.pb + kOffW1; g.sbn = kIn; g.sbk = 1;
   g.M = B; g.N = kHid; g.K = kIn; g.bias = params + kOffB1; g.relu = 1; g.Cb = w.h1;
-  cudaError_t e = gemm(g, s);
+  cudaError_t e = gemm(g, w.status, s);
   if (e != cudaSuccess) return e;
   g = GemmArgs{};
   g.A = w.h1; g.sam = kHid; g.sak = 1;
   g.B = w.pb + kOffW2; g.sbn = kHid; g.sbk = 1;
   g.M = B; g.N = kHid; g.K = kHid; g.bias = params + kOffB2; g.relu = 1; g.Cb = w.h2;
-  if ((e = gemm(g, s)) != cudaSuccess) return e;
+  if ((e = gemm(g, w.status, s)) != cudaSuccess) return e;
   g = GemmArgs{};
   g.A = w.h2; g.sam = kHid; g.sak = 1;
   g.B = w.pb + kOffW3; g.sbn = kHid; g.sbk = 1;
   g.M = B; g.N = kOut; g.K = kHid; g.bias = params + kOffB3; g.Cf = w.out;
-  return gemm(g, s);
+  return gemm(g, w.status, s);
 }
 
 // Gradient of the mean loss over the batch into w.grad (FP32), loss sum into w.loss[0].
@@ -380,33 +303,33 @@ static cudaError_t mlp_backward(const ProposalShape& q, const MlpWs& w, int B, c
   g.A = w.dout_b; g.sam = 1; g.sak = kOut;
   g.B = w.h2; g.sbn = 1; g.sbk = kHid;
   g.M = kOut; g.N = kHid; g.K = B; g.Cf = w.grad + kOffW3;
-  if ((e = gemm(g, s)) != cudaSuccess) return e;
+  if ((e = gemm(g, w.status, s)) != cudaSuccess) return e;
   colsum_kernel<float><<<1, 64, 0, s>>>(w.dout, B, kOut, w.grad + kOffB3);
   // dh2[b, i] = sum_o dout[b, o] W3[o, i], masked by h2 > 0
   g = GemmArgs{};
   g.A = w.dout_b; g.sam = kOut; g.sak = 1;
   g.B = w.pb + kOffW3; g.sbn = 1; g.sbk = kHid;
   g.M = B; g.N = kHid; g.K = kOut; g.mask = w.h2; g.Cb = w.dh2;
-  if ((e = gemm(g, s)) != cudaSuccess) return e;
+  if ((e = gemm(g, w.status, s)) != cudaSuccess) return e;
   // dW2[o, i] = sum_b dh2[b, o] h1[b, i]
   g = GemmArgs{};
   g.A = w.dh2; g.sam = 1; g.sak = kHid;
   g.B = w.h1; g.sbn = 1; g.sbk = kHid;
   g.M = kHid; g.N = kHid; g.K = B; g.Cf = w.grad + kOffW2;
-  if ((e = gemm(g, s)) != cudaSuccess) return e;
+  if ((e = gemm(g, w.status, s)) != cudaSuccess) return e;
   colsum_kernel<__nv_bfloat16><<<1, kHid, 0, s>>>(w.dh2, B, kHid, w.grad + kOffB2);
   // dh1 = (dh2 W2) masked by h1 > 0
   g = GemmArgs{};
   g.A = w.dh2; g.sam = kHid; g.sak = 1;
   g.B = w.pb + kOffW2; g.sbn = 1; g.sbk = kHid;
   g.M = B; g.N = kHid; g.K = kHid; g.mask = w.h1; g.Cb = w.dh1;
-  if ((e = gemm(g, s)) != cudaSuccess) return e;
+  if ((e = gemm(g, w.status, s)) != cudaSuccess) return e;
   // dW1[o, i] = sum_b dh1[b, o] feat[b, i]
   g = GemmArgs{};
   g.A = w.dh1; g.sam = 1; g.sak = kHid;
   g.B = w.feat; g.sbn = 1; g.sbk = kIn;
   g.M = kHid; g.N = kIn; g.K = B; g.Cf = w.grad + kOffW1;
-  if ((e = gemm(g, s)) != cudaSuccess) return e;
+  if ((e = gemm(g, w.status, s)) != cudaSuccess) return e;
   colsum_kernel<__nv_bfloat16><<<1, kHid, 0, s>>>(w.dh1, B, kHid, w.grad + kOffB1);
   return cudaGetLastError();
 }
@@ -468,6 +391,7 @@ ppl_status ppl_proposal_forward(const ppl_model* model, const float* params, con
   MlpWs w = mlp_ws(static_cast<char*>(ws), n_sets);
   if (ws_bytes < w.total) return PPL_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(w.status, 0, sizeof(int32_t), s) != cudaSuccess) return PPL_ECUDA;
   to_bf16_kernel<<<(unsigned)((kNumParams + kTpb - 1) / kTpb), kTpb, 0, s>>>(params, w.pb,
                                                                             kNumParams);
   features_kernel<<<(unsigned)(((int64_t)n_sets * 32 + kTpb - 1) / kTpb), kTpb, 0, s>>>(
@@ -495,6 +419,7 @@ ppl_status ppl_proposal_grad(const ppl_model* model, const float* params, int64_
   MlpWs w = mlp_ws(static_cast<char*>(ws), batch);
   if (ws_bytes < w.total) return PPL_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(w.status, 0, sizeof(int32_t), s) != cudaSuccess) return PPL_ECUDA;
   to_bf16_kernel<<<(unsigned)((kNumParams + kTpb - 1) / kTpb), kTpb, 0, s>>>(params, w.pb,
                                                                             kNumParams);
   forward_sim_kernel<<<(unsigned)(((int64_t)batch * 32 + kTpb - 1) / kTpb), kTpb, 0, s>>>(
@@ -522,6 +447,7 @@ ppl_status ppl_proposal_train(const ppl_model* model, float* params, float* adam
   MlpWs w = mlp_ws(static_cast<char*>(ws), batch);
   if (ws_bytes < w.total) return PPL_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(w.status, 0, sizeof(int32_t), s) != cudaSuccess) return PPL_ECUDA;
   const ProposalShape q = shape_of(p, model->prior_sigma);
   const int64_t steps_per_epoch = n_pairs / batch;
   if (cudaMemsetAsync(w.step, 0, sizeof(int32_t), s) != cudaSuccess) return PPL_ECUDA;
