@@ -36,6 +36,7 @@ struct UmmaArgs {
   float* Cf;          // FP32 output [M x N], optional
   __nv_bfloat16* Cb;  // BF16 output [M x N], optional
   int32_t* status;    // set to PPL_ETIMEOUT when a wait runs out
+  int vec_a, vec_b;   // K contiguous, rows 16-byte aligned: 8 elements per load
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -102,15 +103,37 @@ __global__ void __launch_bounds__(128) umma_gemm_kernel(UmmaArgs g) {
   bool any = false;
   for (int k0 = 0; k0 < g.K; k0 += kUK) {
     // stage the K tile (the previous tile's MMAs have completed)
-    for (int e = tid; e < kUM * kUK; e += 128) {
-      const int r = e / kUK, k = e % kUK;
-      const int gm = m0 + r, gk = k0 + k;
-      As[core_index(r, k)] = (gm < g.M && gk < g.K) ? g.A[gm * g.sam + gk * g.sak] : zero;
+    if (g.vec_a) {  // one core-matrix row (8 consecutive k) per 16-byte load
+      for (int e = tid; e < kUM * (kUK / 8); e += 128) {
+        const int r = e / (kUK / 8), k = (e % (kUK / 8)) * 8;
+        const int gm = m0 + r, gk = k0 + k;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (gm < g.M && gk < g.K)  // K % 8 == 0: the whole row is in range
+          v = *reinterpret_cast<const uint4*>(g.A + (int64_t)gm * g.sam + gk);
+        *reinterpret_cast<uint4*>(As + core_index(r, k)) = v;
+      }
+    } else {
+      for (int e = tid; e < kUM * kUK; e += 128) {
+        const int r = e / kUK, k = e % kUK;
+        const int gm = m0 + r, gk = k0 + k;
+        As[core_index(r, k)] = (gm < g.M && gk < g.K) ? g.A[gm * g.sam + gk * g.sak] : zero;
+      }
     }
-    for (int e = tid; e < kUN * kUK; e += 128) {
-      const int r = e / kUK, k = e % kUK;
-      const int gn = n0 + r, gk = k0 + k;
-      Bs[core_index(r, k)] = (gn < g.N && gk < g.K) ? g.B[gn * g.sbn + gk * g.sbk] : zero;
+    if (g.vec_b) {
+      for (int e = tid; e < kUN * (kUK / 8); e += 128) {
+        const int r = e / (kUK / 8), k = (e % (kUK / 8)) * 8;
+        const int gn = n0 + r, gk = k0 + k;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (gn < g.N && gk < g.K)
+          v = *reinterpret_cast<const uint4*>(g.B + (int64_t)gn * g.sbn + gk);
+        *reinterpret_cast<uint4*>(Bs + core_index(r, k)) = v;
+      }
+    } else {
+      for (int e = tid; e < kUN * kUK; e += 128) {
+        const int r = e / kUK, k = e % kUK;
+        const int gn = n0 + r, gk = k0 + k;
+        Bs[core_index(r, k)] = (gn < g.N && gk < g.K) ? g.B[gn * g.sbn + gk * g.sbk] : zero;
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // visible to the tensor cores
     __syncthreads();
@@ -196,6 +219,10 @@ cudaError_t launch_umma_gemm(const __nv_bfloat16* A, int64_t sam, int64_t sak,
   g.B = B; g.sbn = sbn; g.sbk = sbk;
   g.M = M; g.N = N; g.K = K;
   g.bias = bias; g.mask = mask; g.relu = relu; g.Cf = Cf; g.Cb = Cb; g.status = status;
+  // 16-byte loads need K contiguous, K and the row stride multiples of 8, and
+  // a 16-byte aligned base
+  g.vec_a = sak == 1 && K % 8 == 0 && sam % 8 == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
+  g.vec_b = sbk == 1 && K % 8 == 0 && sbn % 8 == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0;
   dim3 grid((N + kUN - 1) / kUN, (M + kUM - 1) / kUM);
   umma_gemm_kernel<<<grid, 128, kUmmaSmem, s>>>(g);
   return cudaGetLastError();
