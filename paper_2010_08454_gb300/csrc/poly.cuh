@@ -36,68 +36,15 @@ __device__ __forceinline__ int poly_draw(const PolyParams& p, uint64_t seed, uin
   return n;
 }
 
-// The factor of PPT traces over `len` data points staged in shared memory:
-// ss += sum_l (y_l - f(x_l))^2 with f by Horner's rule, six coefficients (the
-// zero padding past a trace's count leaves the value unchanged).
+// Compensated (Kahan) addition: the factor sums of the trace kernels add their
+// 16-point inner sums this way, which keeps the FP32 accumulation error at a
+// few ulps.
 __device__ __forceinline__ void kahan_add(float& sum, float& comp, float v) {
   const float y = __fsub_rn(v, comp);
   const float t = __fadd_rn(sum, y);
   comp = __fsub_rn(__fsub_rn(t, sum), y);
   sum = t;
 }
-
-template <int PPT>
-__device__ __forceinline__ void accumulate_points(const float2* sdata, int len,
-                                                  const float (&c)[PPT][kMaxCoef],
-                                                  float (&ss)[PPT], float (&comp)[PPT]) {
-  // Inner sums over 16 points, combined by a compensated sum, keep the FP32
-  // accumulation error at a few ulps.
-  int l = 0;
-  for (; l + 16 <= len; l += 16) {
-    float part[PPT];
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) part[q] = 0.0f;
-#pragma unroll 4
-    for (int j = 0; j < 16; ++j) {
-      const float2 d = sdata[l + j];
-#pragma unroll
-      for (int q = 0; q < PPT; ++q) {
-        float f = c[q][5];
-        f = fmaf(f, d.x, c[q][4]);
-        f = fmaf(f, d.x, c[q][3]);
-        f = fmaf(f, d.x, c[q][2]);
-        f = fmaf(f, d.x, c[q][1]);
-        f = fmaf(f, d.x, c[q][0]);
-        const float r = d.y - f;
-        part[q] = fmaf(r, r, part[q]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) kahan_add(ss[q], comp[q], part[q]);
-  }
-  if (l < len) {
-    float part[PPT];
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) part[q] = 0.0f;
-    for (; l < len; ++l) {
-      const float2 d = sdata[l];
-#pragma unroll
-      for (int q = 0; q < PPT; ++q) {
-        float f = c[q][5];
-        f = fmaf(f, d.x, c[q][4]);
-        f = fmaf(f, d.x, c[q][3]);
-        f = fmaf(f, d.x, c[q][2]);
-        f = fmaf(f, d.x, c[q][1]);
-        f = fmaf(f, d.x, c[q][0]);
-        const float r = d.y - f;
-        part[q] = fmaf(r, r, part[q]);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < PPT; ++q) kahan_add(ss[q], comp[q], part[q]);
-  }
-}
-
 
 // Running log-sum-exp statistics of one thread / block: maximum and its
 // (lowest) index, sums of exp(lw - m) and exp(2 (lw - m)), and the best trace

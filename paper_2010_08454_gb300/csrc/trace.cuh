@@ -5,11 +5,12 @@
 // performance (§5.1).  Here the block first draws every trace's degree and
 // coefficients (counter-addressed, so independent of order), sorts the group
 // by degree with a deterministic counting sort in shared memory, and lets each
-// warp evaluate 128 consecutive sorted traces with a Horner chain specialised
-// to the warp's largest coefficient count.  Warps are then uniform except the
-// few that straddle two degrees, which pad the shorter traces with zero
-// coefficients (the same value exactly).  Each degree is a contiguous bucket of
-// the sorted group, reduced by one warp into a per-degree partial.
+// warp evaluate rows of consecutive sorted traces with Horner chains
+// specialised to each row's largest coefficient count.  Rows are uniform
+// except the few that straddle two degrees, which pad the shorter traces with
+// zero coefficients (the same value exactly).  Each warp pairs a row from the
+// low-degree end of the sort with one from the high-degree end, so the warps
+// of a block do nearly equal work and seldom wait at the group's barriers.
 #pragma once
 
 #include "posterior.cuh"
@@ -17,10 +18,9 @@
 
 namespace ppl {
 
-
-constexpr int kCStride = 7;
+constexpr int kCStride = 7;         // shared-memory stride of a trace's coefficients (odd: no bank conflicts)
 constexpr float kSkipNats = 50.0f;  // traces this far below their degree's running maximum are skipped
-constexpr int kSerialMerges = 4;    // up to this many traces a warp merges one at a time  // shared-memory stride of a trace's coefficients (odd: no bank conflicts)
+constexpr int kSerialMerges = 4;    // up to this many traces a warp merges one at a time
 
 // Shared memory of one group of kTpb * PPT traces.
 template <int PPT>
@@ -189,6 +189,138 @@ __device__ __forceinline__ void accumulate_dispatch(int nc, const float2* sdata,
   }
 }
 
+// One pass over the staged points for traces J0 .. J0 + 3 as two f32x2 pairs
+// with their own Horner lengths: (J0, J0 + 1) over NCA coefficients and
+// (J0 + 2, J0 + 3) over NCB (NCB = 0: the second pair has no traces).  The
+// per-trace arithmetic is that of accumulate_nc, bit for bit.
+template <int PPT, int J0, int NCA, int NCB>
+__device__ __forceinline__ void accumulate_two(const float2* sdata, int len,
+                                               const float (&c)[PPT][kMaxCoef], float (&ss)[PPT],
+                                               float (&comp)[PPT]) {
+  static_assert(NCA >= 1 && (NCB == 0 || NCB >= NCA) && J0 + 3 < PPT, "sorted pair rows");
+  constexpr int NB = NCB > 0 ? NCB : 1;
+  unsigned long long ca[NCA], cb[NB];
+#pragma unroll
+  for (int k = 0; k < NCA; ++k) ca[k] = f2_pack(c[J0][k], c[J0 + 1][k]);
+#pragma unroll
+  for (int k = 0; k < NB; ++k) cb[k] = f2_pack(c[J0 + 2][k], c[J0 + 3][k]);
+  int l = 0;
+  while (l < len) {
+    const int n = (len - l) < 16 ? (len - l) : 16;
+    unsigned long long pa = 0ull, pb = 0ull;  // +0.0f in both halves
+#pragma unroll 4
+    for (int j = 0; j < n; ++j) {
+      const float2 d = sdata[l + j];
+      const unsigned long long xx = f2_pack(d.x, d.x), yy = f2_pack(d.y, d.y);
+      unsigned long long f = ca[NCA - 1];
+#pragma unroll
+      for (int k = NCA - 2; k >= 0; --k) f = f2_fma(f, xx, ca[k]);
+      const unsigned long long r = f2_sub(yy, f);
+      pa = f2_fma(r, r, pa);
+      if constexpr (NCB > 0) {
+        unsigned long long g = cb[NCB - 1];
+#pragma unroll
+        for (int k = NCB - 2; k >= 0; --k) g = f2_fma(g, xx, cb[k]);
+        const unsigned long long t = f2_sub(yy, g);
+        pb = f2_fma(t, t, pb);
+      }
+    }
+    const float2 va = f2_unpack(pa);
+    kahan_add(ss[J0], comp[J0], va.x);
+    kahan_add(ss[J0 + 1], comp[J0 + 1], va.y);
+    if constexpr (NCB > 0) {
+      const float2 vb = f2_unpack(pb);
+      kahan_add(ss[J0 + 2], comp[J0 + 2], vb.x);
+      kahan_add(ss[J0 + 3], comp[J0 + 3], vb.y);
+    }
+    l += n;
+  }
+}
+
+template <int PPT, int J0, int NCA>
+__device__ __forceinline__ void accumulate_two_b(int ncb, const float2* sdata, int len,
+                                                 const float (&c)[PPT][kMaxCoef],
+                                                 float (&ss)[PPT], float (&comp)[PPT]) {
+  // ncb >= NCA by the sorted order, or 0 when the second pair row is empty
+  switch (ncb) {
+    case 0: accumulate_two<PPT, J0, NCA, 0>(sdata, len, c, ss, comp); break;
+    case 1:
+      if constexpr (NCA <= 1) accumulate_two<PPT, J0, NCA, 1>(sdata, len, c, ss, comp);
+      break;
+    case 2:
+      if constexpr (NCA <= 2) accumulate_two<PPT, J0, NCA, 2>(sdata, len, c, ss, comp);
+      break;
+    case 3:
+      if constexpr (NCA <= 3) accumulate_two<PPT, J0, NCA, 3>(sdata, len, c, ss, comp);
+      break;
+    case 4:
+      if constexpr (NCA <= 4) accumulate_two<PPT, J0, NCA, 4>(sdata, len, c, ss, comp);
+      break;
+    case 5:
+      if constexpr (NCA <= 5) accumulate_two<PPT, J0, NCA, 5>(sdata, len, c, ss, comp);
+      break;
+    default: accumulate_two<PPT, J0, NCA, 6>(sdata, len, c, ss, comp); break;
+  }
+}
+
+// Horner lengths nca <= ncb of the two pair rows (0: the row has no traces).
+template <int PPT, int J0>
+__device__ __forceinline__ void accumulate_two_dispatch(int nca, int ncb, const float2* sdata,
+                                                        int len, const float (&c)[PPT][kMaxCoef],
+                                                        float (&ss)[PPT], float (&comp)[PPT]) {
+  switch (nca) {
+    case 0: break;
+    case 1: accumulate_two_b<PPT, J0, 1>(ncb, sdata, len, c, ss, comp); break;
+    case 2: accumulate_two_b<PPT, J0, 2>(ncb, sdata, len, c, ss, comp); break;
+    case 3: accumulate_two_b<PPT, J0, 3>(ncb, sdata, len, c, ss, comp); break;
+    case 4: accumulate_two_b<PPT, J0, 4>(ncb, sdata, len, c, ss, comp); break;
+    case 5: accumulate_two_b<PPT, J0, 5>(ncb, sdata, len, c, ss, comp); break;
+    default: accumulate_two_b<PPT, J0, 6>(ncb, sdata, len, c, ss, comp); break;
+  }
+}
+
+// Sorted slot of trace j of a lane.  With four or more traces per thread the
+// sorted group is cut into pair rows of 64 slots (32 lanes x an f32x2 pair),
+// and warp w takes pair rows w and 2W - 1 - w (then 2W + w and 4W - 1 - w): a
+// row from the low-degree end of the sort with one from the high-degree end,
+// so that the warps of a block do about equal work between its barriers.
+// With fewer, warp w takes the 32 PPT consecutive slots from 32 PPT w.
+template <int PPT>
+__device__ __forceinline__ int sorted_slot(int warp, int lane, int j) {
+  constexpr int W = kTpb / 32;
+  if constexpr (PPT % 4 == 0) {
+    const int p = j >> 1, r = p * W + ((p & 1) ? W - 1 - warp : warp);
+    return 64 * r + 32 * (j & 1) + lane;
+  } else {
+    return warp * 32 * PPT + 32 * j + lane;
+  }
+}
+
+// Degree index of a sorted slot, from the bucket offsets.
+__device__ __forceinline__ int slot_degree(const int* off, int s) {
+  int dk = 0;
+#pragma unroll
+  for (int k = 1; k < kMaxDegrees; ++k)
+    if (s >= off[k]) dk = k;
+  return dk;
+}
+
+// The factor sums of a lane's PPT traces over `len` staged points; nc[u] is
+// the Horner length of the lane's u-th row group (pair row, or the warp's
+// slots when PPT < 4), 0 when it holds no trace.
+template <int PPT>
+__device__ __forceinline__ void accumulate_rows(const int (&nc)[PPT], const float2* sdata,
+                                                int len, const float (&c)[PPT][kMaxCoef],
+                                                float (&ss)[PPT], float (&comp)[PPT]) {
+  if constexpr (PPT % 4 == 0) {
+    accumulate_two_dispatch<PPT, 0>(nc[0], nc[1], sdata, len, c, ss, comp);
+    if constexpr (PPT == 8) accumulate_two_dispatch<PPT, 4>(nc[2], nc[3], sdata, len, c, ss, comp);
+    static_assert(PPT <= 8, "at most two passes");
+  } else {
+    if (nc[0] > 0) accumulate_dispatch<PPT>(nc[0], sdata, len, c, ss, comp);
+  }
+}
+
 // Draw policy of the prior (§3.4 `sample` from the model's own distributions):
 // log-weight correction 0.
 struct PriorDraw {
@@ -279,47 +411,49 @@ __device__ __forceinline__ void trace_group(const Draw& draw, const PolyParams& 
   __syncthreads();
   const int n_valid = ts.off[kMaxDegrees];
 
-  // B. evaluate: warp w owns sorted slots [128 w, 128 w + 128), lane l the
-  // slots 128 w + 32 j + l; the Horner length is the warp's largest
-  int slot[PPT];
-  const bool active = warp * 32 * PPT < n_valid;
-  const int wlast = min(warp * 32 * PPT + 32 * PPT, n_valid) - 1;
-  int dlast = 0;
-#pragma unroll
-  for (int k = 1; k < kMaxDegrees; ++k)
-    if (wlast >= ts.off[k]) dlast = k;
-  const int nc = p.min_deg + dlast + p.coef_offset;
+  // B. evaluate the lane's sorted slots (sorted_slot); each row group runs a
+  // Horner chain as long as its largest coefficient count
+  int slot[PPT], nc[PPT];
   float ss[PPT], comp[PPT];
 #pragma unroll
   for (int j = 0; j < PPT; ++j) {
-    slot[j] = warp * 32 * PPT + 32 * j + lane;
+    slot[j] = sorted_slot<PPT>(warp, lane, j);
     ss[j] = 0.0f;
     comp[j] = 0.0f;
 #pragma unroll
     for (int k = 0; k < kMaxCoef; ++k)
       c[j][k] = (slot[j] < n_valid) ? ts.c[slot[j] * kCStride + k] : 0.0f;
   }
+  {
+    constexpr int G = PPT % 4 == 0 ? PPT / 2 : 1;  // row groups of a lane
+    constexpr int span = PPT % 4 == 0 ? 64 : 32 * PPT;
+#pragma unroll
+    for (int u = 0; u < PPT; ++u) {
+      nc[u] = 0;
+      if (u < G) {
+        const int first = sorted_slot<PPT>(warp, 0, PPT % 4 == 0 ? 2 * u : 0);
+        if (first < n_valid) {
+          const int last = min(first + span, n_valid) - 1;
+          nc[u] = max(1, p.min_deg + slot_degree(ts.off, last) + p.coef_offset);
+        }
+      }
+    }
+  }
   if (suff != nullptr && suff->ok) {  // the same branch for the whole block
     // sufficient statistics: O(d^2) per trace, d its own coefficient count
 #pragma unroll
-    for (int j = 0; j < PPT; ++j) {
-      if (slot[j] < n_valid) {
-        int dk = 0;
-#pragma unroll
-        for (int k = 1; k < kMaxDegrees; ++k)
-          if (slot[j] >= ts.off[k]) dk = k;
-        ss[j] = suff_residual(*suff, c[j], p.min_deg + dk + p.coef_offset);
-      }
-    }
+    for (int j = 0; j < PPT; ++j)
+      if (slot[j] < n_valid)
+        ss[j] = suff_residual(*suff, c[j], p.min_deg + slot_degree(ts.off, slot[j]) + p.coef_offset);
   } else if (resident) {
-    if (active) accumulate_dispatch<PPT>(nc, sdata, (int)L, c, ss, comp);
+    accumulate_rows<PPT>(nc, sdata, (int)L, c, ss, comp);
   } else {
     for (int64_t l0 = 0; l0 < L; l0 += chunk) {
       const int len = (int)(L - l0 < (int64_t)chunk ? L - l0 : (int64_t)chunk);
       __syncthreads();
       for (int l = tid; l < len; l += kTpb) sdata[l] = make_float2(xs[l0 + l], ys[l0 + l]);
       __syncthreads();
-      if (active) accumulate_dispatch<PPT>(nc, sdata, len, c, ss, comp);
+      accumulate_rows<PPT>(nc, sdata, len, c, ss, comp);
     }
   }
   // C. each warp folds its traces into its running per-degree partials.  A
@@ -344,10 +478,7 @@ __device__ __forceinline__ void trace_group(const Draw& draw, const PolyParams& 
     if (slot[j] < n_valid) {
       lw[j] = ss[j] * p.neg_half_inv_var + ts.c[slot[j] * kCStride + kMaxCoef];
       if (lw_out) lw_out[ts.idx[slot[j]]] = lw[j];
-      int dj = 0;
-#pragma unroll
-      for (int k = 1; k < kMaxDegrees; ++k)
-        if (slot[j] >= ts.off[k]) dj = k;
+      const int dj = slot_degree(ts.off, slot[j]);
       deg[j] = dj;
       float t = thr[0];
 #pragma unroll
@@ -386,11 +517,14 @@ __device__ __forceinline__ void trace_group(const Draw& draw, const PolyParams& 
       }
     }
   } else if (ncand > kSerialMerges) {
-    int dlo = 0;
+    // the degrees that have candidates in this warp
+    unsigned dmask = 0;
 #pragma unroll
-    for (int k = 1; k < kMaxDegrees; ++k)
-      if (warp * 32 * PPT >= ts.off[k]) dlo = k;
-    for (int dd = dlo; dd <= dlast; ++dd) {
+    for (int j = 0; j < PPT; ++j)
+      if ((cmask[j] >> lane) & 1u) dmask |= 1u << deg[j];
+    dmask = __reduce_or_sync(0xffffffffu, dmask);
+    for (int dd = 0; dd < kMaxDegrees; ++dd) {
+      if (!((dmask >> dd) & 1u)) continue;
       float m = -INFINITY;
       int a = 0x7fffffff, as = -1;
 #pragma unroll
