@@ -286,23 +286,40 @@ __global__ void __launch_bounds__(kTpb) ancestors_kernel(const uint64_t* __restr
 
 // state_out[k] = state_in[anc[k]]: one thread per vector word of the output,
 // so stores are fully coalesced; ancestors are non-decreasing, so loads are
-// nearly so.  Out-of-range ancestors give zero records.
-template <typename V>
+// nearly so.  Out-of-range ancestors give zero records.  W > 0 fixes the words
+// per record at compile time (the index split is then a shift or a constant
+// division); W = 0 reads it from `words`.  Each thread takes kGatherUnroll
+// words per round, so that many ancestor loads are in flight at once.
+constexpr int kGatherUnroll = 4;
+
+template <typename V, int W>
 __global__ void __launch_bounds__(kTpb) gather_kernel(const V* __restrict__ in, int64_t n_in,
-                                                      int64_t words,
+                                                      int64_t words_rt,
                                                       const int32_t* __restrict__ anc,
                                                       int64_t M, V* __restrict__ out,
                                                       const int32_t* gate) {
   if (gate && *gate == 0) return;
+  const int64_t words = W > 0 ? (int64_t)W : words_rt;
   const int64_t total = M * words;
   const int64_t stride = (int64_t)gridDim.x * kTpb;
-  for (int64_t u = (int64_t)blockIdx.x * kTpb + threadIdx.x; u < total; u += stride) {
-    const int64_t k = u / words, v = u - k * words;
-    const int64_t a = anc[k];
-    V val;
-    if (a >= 0 && a < n_in) val = in[a * words + v];
-    else memset(&val, 0, sizeof(V));
-    out[u] = val;
+  for (int64_t u0 = (int64_t)blockIdx.x * kTpb + threadIdx.x; u0 < total;
+       u0 += stride * kGatherUnroll) {
+    int64_t a[kGatherUnroll];
+#pragma unroll
+    for (int r = 0; r < kGatherUnroll; ++r) {
+      const int64_t u = u0 + r * stride;
+      a[r] = u < total ? (int64_t)anc[u / words] : -1;
+    }
+#pragma unroll
+    for (int r = 0; r < kGatherUnroll; ++r) {
+      const int64_t u = u0 + r * stride;
+      if (u >= total) break;
+      const int64_t v = u % words;
+      V val;
+      if (a[r] >= 0 && a[r] < n_in) val = in[a[r] * words + v];
+      else memset(&val, 0, sizeof(V));
+      out[u] = val;
+    }
   }
 }
 
@@ -355,25 +372,30 @@ cudaError_t launch_ancestors(const uint64_t* prefix, int64_t N, int64_t M, const
   return cudaGetLastError();
 }
 
+template <typename V>
+static void launch_gather_t(const V* in, int64_t n_in, int64_t words, const int32_t* anc,
+                            int64_t M, V* out, const int32_t* gate, cudaStream_t s) {
+  const int64_t cap = (int64_t)num_sms() * 8;
+  const int64_t want = (M * words + (int64_t)kTpb * kGatherUnroll - 1) / ((int64_t)kTpb * kGatherUnroll);
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, cap));
+  switch (words) {
+    case 1: gather_kernel<V, 1><<<grid, kTpb, 0, s>>>(in, n_in, words, anc, M, out, gate); break;
+    case 2: gather_kernel<V, 2><<<grid, kTpb, 0, s>>>(in, n_in, words, anc, M, out, gate); break;
+    case 4: gather_kernel<V, 4><<<grid, kTpb, 0, s>>>(in, n_in, words, anc, M, out, gate); break;
+    default: gather_kernel<V, 0><<<grid, kTpb, 0, s>>>(in, n_in, words, anc, M, out, gate); break;
+  }
+}
+
 cudaError_t launch_gather(const void* in, int64_t n_in, int64_t stride_bytes, const int32_t* anc,
                           int64_t M, void* out, const int32_t* gate, cudaStream_t s) {
   const uintptr_t a = reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out);
-  const int64_t cap = (int64_t)num_sms() * 8;
-  if (stride_bytes % 16 == 0 && (a & 15) == 0) {
-    const int64_t words = stride_bytes / 16;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((M * words + kTpb - 1) / kTpb, cap));
-    gather_kernel<uint4><<<grid, kTpb, 0, s>>>((const uint4*)in, n_in, words, anc, M, (uint4*)out, gate);
-  } else if (stride_bytes % 4 == 0 && (a & 3) == 0) {
-    const int64_t words = stride_bytes / 4;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((M * words + kTpb - 1) / kTpb, cap));
-    gather_kernel<uint32_t><<<grid, kTpb, 0, s>>>((const uint32_t*)in, n_in, words, anc, M,
-                                                 (uint32_t*)out, gate);
-  } else {
-    const int64_t words = stride_bytes;
-    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((M * words + kTpb - 1) / kTpb, cap));
-    gather_kernel<uint8_t><<<grid, kTpb, 0, s>>>((const uint8_t*)in, n_in, words, anc, M,
-                                                (uint8_t*)out, gate);
-  }
+  if (stride_bytes % 16 == 0 && (a & 15) == 0)
+    launch_gather_t<uint4>((const uint4*)in, n_in, stride_bytes / 16, anc, M, (uint4*)out, gate, s);
+  else if (stride_bytes % 4 == 0 && (a & 3) == 0)
+    launch_gather_t<uint32_t>((const uint32_t*)in, n_in, stride_bytes / 4, anc, M, (uint32_t*)out,
+                              gate, s);
+  else
+    launch_gather_t<uint8_t>((const uint8_t*)in, n_in, stride_bytes, anc, M, (uint8_t*)out, gate, s);
   return cudaGetLastError();
 }
 

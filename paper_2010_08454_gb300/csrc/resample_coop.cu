@@ -3,24 +3,28 @@
 // a_k = min{j : C_j > u + k stride}) in one persistent, cooperative kernel
 // with one grid barrier, and no prefix-sum array in global memory:
 //
-//   1. the particles are cut into chunks of 8192; blocks sum the weights of
-//      their chunks (one read of lw);
+//   1. the particles are cut into chunks of 4096; blocks sum the weights of
+//      their chunks (one read of lw), with one block barrier per 32 chunks;
 //   2. barrier: the last arriving block scans the chunk totals, draws u, and
 //      gives every chunk its first output K_c = #{k : u + k stride < C_start}
 //      -- chunk c holds the ancestors of outputs [K_c, K_c+1) -- and cuts each
-//      chunk's outputs into work items of at most 8192;
-//   3. blocks take the items in turn: an item forms its chunk's inclusive
-//      prefix sums in shared memory (lw is L2-resident by now) and finds its
-//      outputs' ancestors by merging the sorted prefix sums with the sorted
-//      positions (merge path: Green, McColl, Bader, "GPU merge path", ICS
-//      2012), one equal slice of the merge per thread.
+//      chunk's outputs into work items of at most 256;
+//   3. each block takes a contiguous run of items (weighted so that a chunk's
+//      prefix sums count as a number of items); for each chunk the run
+//      touches, the block forms the chunk's inclusive prefix sums in shared
+//      memory (lw is L2-resident by now) with a two-level index of every 8th
+//      and every 256th sum, and then its warps take the chunk's items
+//      independently: a warp finds the item's range of candidate ancestors by
+//      three 32-way probes of the index, and its lanes merge those prefix sums
+//      with the item's sorted positions (merge path: Green, McColl, Bader, "GPU
+//      merge path", ICS 2012), one equal slice of the merge per lane.
 //
-// Every item costs at most 8192 weights and 8192 outputs whatever the
-// weights are: a chunk holding most of the mass (degenerate importance
-// weights) becomes many items on many blocks.  The ancestors are those of the
-// scan-and-search path bit for bit (both are exact integer computations of the
-// same definition).  Traffic: lw twice (the second time from L2), the
-// ancestors once.
+// Every item costs at most 4096 weights and 256 outputs whatever the weights
+// are: a chunk holding most of the mass (degenerate importance weights)
+// becomes many items on many blocks and warps, with no block barrier between
+// them.  The ancestors are those of the scan-and-search path bit for bit (both
+// are exact integer computations of the same definition).  Traffic: lw twice
+// (the second time from L2), the ancestors once.
 #include <algorithm>
 
 #include "gridsync.cuh"
@@ -29,10 +33,17 @@
 
 namespace ppl {
 
-constexpr int kRcTpb = 1024;                          // one block per SM
+constexpr int kRcTpb = 512;                           // two blocks per SM
+constexpr int kRcWarps = kRcTpb / 32;
 constexpr int kRcItems = 8;                           // weights per thread per chunk
 constexpr int64_t kRcChunk = (int64_t)kRcTpb * kRcItems;
-constexpr int64_t kRcItemOut = 8192;                  // outputs of one work item
+constexpr int kRcItemOut = 256;                       // outputs of one work item (one warp)
+constexpr int kRcBatch = 32;                          // chunks summed between block barriers
+// A chunk's prefix sums cost a block about as much time as this many work
+// items; every chunk with outputs is charged it in the partition of the
+// items over the blocks, so that a block whose run crosses many sparsely
+// used chunks takes correspondingly fewer items.
+constexpr int kRcPrefixCost = 64;
 
 struct RcArgs {
   const float* lw;         // FP32 log-weights, or
@@ -51,43 +62,113 @@ struct RcArgs {
   int64_t* ioff;    // [n_chunks + 1] first work item of each chunk
 };
 
+// The weights of one thread's kRcItems particles from `base`: FP32
+// log-weights (raw, -inf past n) or given fixed-point words (0 past n).
 template <bool FROM_LW>
-__device__ __forceinline__ void load_weights(const RcArgs& a, int64_t base, float m_lw, float scale,
-                                             uint64_t (&q)[kRcItems], int& bad) {
-  if (FROM_LW) {
-    float v[kRcItems];
+struct RawWeights {
+  float v[kRcItems];
+};
+template <>
+struct RawWeights<false> {
+  uint64_t v[kRcItems];
+};
+
+template <bool FROM_LW>
+__device__ __forceinline__ void load_raw(const RcArgs& a, int64_t base, RawWeights<FROM_LW>& w) {
+  if constexpr (FROM_LW) {
     if (base + kRcItems <= a.n && (reinterpret_cast<uintptr_t>(a.lw + base) & 15) == 0) {
       const float4 x = __ldcg(reinterpret_cast<const float4*>(a.lw + base));
       const float4 y = __ldcg(reinterpret_cast<const float4*>(a.lw + base) + 1);
-      v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
-      v[4] = y.x; v[5] = y.y; v[6] = y.z; v[7] = y.w;
+      w.v[0] = x.x; w.v[1] = x.y; w.v[2] = x.z; w.v[3] = x.w;
+      w.v[4] = y.x; w.v[5] = y.y; w.v[6] = y.z; w.v[7] = y.w;
     } else {
 #pragma unroll
-      for (int r = 0; r < kRcItems; ++r) v[r] = base + r < a.n ? __ldcg(a.lw + base + r) : -INFINITY;
+      for (int r = 0; r < kRcItems; ++r)
+        w.v[r] = base + r < a.n ? __ldcg(a.lw + base + r) : -INFINITY;
     }
-#pragma unroll
-    for (int r = 0; r < kRcItems; ++r) q[r] = quantize(v[r], m_lw, scale);
   } else {
 #pragma unroll
-    for (int r = 0; r < kRcItems; ++r) {
-      const uint64_t x = base + r < a.n ? __ldcg(a.qf + base + r) : 0ull;
-      bad |= x > (1ull << 61);
-      q[r] = x > kLimit ? kLimit : x;
+    for (int r = 0; r < kRcItems; ++r) w.v[r] = base + r < a.n ? __ldcg(a.qf + base + r) : 0ull;
+  }
+}
+
+// Fixed-point weights from raw ones (log-weights quantised against m_lw).
+template <bool FROM_LW>
+__device__ __forceinline__ void to_fixed(const RawWeights<FROM_LW>& w, float m_lw, float scale,
+                                         uint64_t (&q)[kRcItems], int& bad) {
+#pragma unroll
+  for (int r = 0; r < kRcItems; ++r) {
+    if constexpr (FROM_LW) {
+      q[r] = quantize(w.v[r], m_lw, scale);
+    } else {
+      bad |= w.v[r] > (1ull << 61);
+      q[r] = w.v[r] > kLimit ? kLimit : w.v[r];
     }
   }
 }
 
 template <bool FROM_LW>
-__global__ void __launch_bounds__(kRcTpb, 1) resample_coop_kernel(RcArgs a) {
+__device__ __forceinline__ void load_weights(const RcArgs& a, int64_t base, float m_lw, float scale,
+                                             uint64_t (&q)[kRcItems], int& bad) {
+  RawWeights<FROM_LW> w;
+  load_raw<FROM_LW>(a, base, w);
+  to_fixed<FROM_LW>(w, m_lw, scale, q, bad);
+}
+
+__device__ __forceinline__ uint64_t warp_sum_sat(uint64_t v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = sat_add(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// First j in [lo, hi) with v[j] > x, by one warp over a sorted global array
+// (hi if none): each round the 32 lanes probe 32 evenly spaced entries.
+__device__ __forceinline__ int64_t warp_first_above(const int64_t* v, int64_t lo, int64_t hi,
+                                                    int64_t x, int lane) {
+  while (hi - lo > 32) {
+    const int64_t step = (hi - lo + 31) / 32;
+    const int64_t q = lo + (int64_t)(lane + 1) * step - 1;
+    const unsigned m = __ballot_sync(0xffffffffu, q >= hi || __ldcg(v + q) > x);
+    if (m == 0) return hi;  // every probe below hi holds <= x, lane 31 probes hi - 1
+    const int f = __ffs(m) - 1;
+    const int64_t qf = lo + (int64_t)(f + 1) * step - 1;
+    lo = lo + (int64_t)f * step;  // probe f - 1 holds <= x
+    hi = qf < hi ? qf : hi;       // the answer is at most probe f
+  }
+  const int64_t q = lo + lane;
+  const unsigned m = __ballot_sync(0xffffffffu, q < hi && __ldcg(v + q) > x);
+  return m ? lo + __ffs(m) - 1 : hi;
+}
+
+// First index of the chunk's prefix sums sA[0..kRcChunk) above x, by one
+// warp, for x below the chunk's last sum: the first 256-block whose last sum
+// is above x (L1: every 256th sum), then the first 8-block within it (L2:
+// every 8th), then the entry.  Each probe reads at most 32 consecutive words.
+__device__ __forceinline__ int chunk_first_above(const uint64_t* sA, const uint64_t* sL2,
+                                                 const uint64_t* sL1, uint64_t x, int lane) {
+  constexpr int nL1 = (int)(kRcChunk / 256);
+  static_assert(kRcChunk % 256 == 0 && nL1 <= 32, "three levels of at most 32");
+  unsigned m = __ballot_sync(0xffffffffu, lane < nL1 && sL1[lane < nL1 ? lane : 0] > x);
+  const int f1 = m ? __ffs(m) - 1 : nL1 - 1;
+  m = __ballot_sync(0xffffffffu, sL2[32 * f1 + lane] > x);
+  const int t = 8 * (32 * f1 + (m ? __ffs(m) - 1 : 31));
+  m = __ballot_sync(0xffffffffu, lane < 8 && sA[t + (lane & 7)] > x);
+  return t + (m ? __ffs(m) - 1 : 7);
+}
+
+template <bool FROM_LW>
+__global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
   if (a.gate && *a.gate == 0) return;  // every block reads the same flag
   extern __shared__ __align__(16) unsigned char rc_dyn[];
-  uint64_t* sA = reinterpret_cast<uint64_t*>(rc_dyn);         // [kRcChunk] prefix sums of a chunk
-  int32_t* sO = reinterpret_cast<int32_t*>(sA + kRcChunk);    // [kRcItemOut] an item's ancestors
-  __shared__ uint64_t wtot[kRcTpb / 32], jtot[kRcTpb / 32];
-  __shared__ int64_t jitem[kRcTpb / 32];
+  uint64_t* sA = reinterpret_cast<uint64_t*>(rc_dyn);  // [kRcChunk] prefix sums of a chunk
+  uint64_t* sL2 = sA + kRcChunk;                        // [kRcTpb] every 8th of them
+  int32_t* sW = reinterpret_cast<int32_t*>(sL2 + kRcTpb);  // [warp][kRcItemOut] ancestors
+  __shared__ uint64_t sL1[kRcChunk / 256];  // every 256th prefix sum
+  __shared__ uint64_t wtot[kRcWarps], jtot[kRcWarps];
+  __shared__ int64_t jitem[kRcWarps];
   __shared__ unsigned long long rel;
   __shared__ uint64_t view[3];  // T, stride, u
-  __shared__ int64_t item_sh[5];  // chunk, C at its start, first and end output, new chunk
+  __shared__ int64_t seg_sh[6];  // chunk, its first item, end item, first and end output, C at its start
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned G = gridDim.x;
   float m_lw = 0.0f, scale = 0.0f;
@@ -98,21 +179,44 @@ __global__ void __launch_bounds__(kRcTpb, 1) resample_coop_kernel(RcArgs a) {
     scale = __int_as_float((127 + 61 - S) << 23);  // 2^(61 - ceil(log2 n))
   }
 
-  // 1. chunk totals
+  // 1. chunk totals: block b sums chunks b, b + G, ...; warps leave their
+  // partial sums of up to kRcBatch chunks in shared memory (aliasing sW), two
+  // chunks' loads in flight per thread, and warp r then adds chunk r's
   int bad = 0;
-  for (int64_t ch = blockIdx.x; ch < a.n_chunks; ch += G) {
-    uint64_t q[kRcItems];
-    load_weights<FROM_LW>(a, ch * kRcChunk + (int64_t)tid * kRcItems, m_lw, scale, q, bad);
-    uint64_t tot = 0;
+  {
+    uint64_t* wt = reinterpret_cast<uint64_t*>(sW);  // [kRcBatch][kRcWarps]
+    static_assert(kRcBatch * kRcWarps * 8 <= kRcWarps * kRcItemOut * 4, "fits in sW");
+    const int64_t nk = a.n_chunks > (int64_t)blockIdx.x
+                           ? (a.n_chunks - (int64_t)blockIdx.x + G - 1) / G : 0;
+    for (int64_t k0 = 0; k0 < nk; k0 += kRcBatch) {
+      const int nb = (int)(nk - k0 < kRcBatch ? nk - k0 : kRcBatch);
+      for (int r = 0; r < nb; r += 2) {
+        const int64_t c0 = (int64_t)blockIdx.x + (k0 + r) * G;
+        RawWeights<FROM_LW> w0, w1;
+        load_raw<FROM_LW>(a, c0 * kRcChunk + (int64_t)tid * kRcItems, w0);
+        if (r + 1 < nb) load_raw<FROM_LW>(a, (c0 + G) * kRcChunk + (int64_t)tid * kRcItems, w1);
+        uint64_t q[kRcItems], t0 = 0, t1 = 0;
+        to_fixed<FROM_LW>(w0, m_lw, scale, q, bad);
 #pragma unroll
-    for (int r = 0; r < kRcItems; ++r) tot = sat_add(tot, q[r]);
-    const uint64_t wi = warp_scan_u64(tot, lane);
-    __syncthreads();  // wtot of the previous chunk is read
-    if (lane == 31) wtot[warp] = wi;
-    __syncthreads();
-    if (warp == 0) {
-      const uint64_t bt = warp_scan_u64(wtot[lane], lane);
-      if (lane == 31) a.ctot[ch] = bt;
+        for (int i = 0; i < kRcItems; ++i) t0 = sat_add(t0, q[i]);
+        if (r + 1 < nb) {
+          to_fixed<FROM_LW>(w1, m_lw, scale, q, bad);
+#pragma unroll
+          for (int i = 0; i < kRcItems; ++i) t1 = sat_add(t1, q[i]);
+        }
+        t0 = warp_sum_sat(t0);
+        t1 = warp_sum_sat(t1);
+        if (lane == 0) {
+          wt[r * kRcWarps + warp] = t0;
+          if (r + 1 < nb) wt[(r + 1) * kRcWarps + warp] = t1;
+        }
+      }
+      __syncthreads();
+      for (int r = warp; r < nb; r += kRcWarps) {
+        const uint64_t t = warp_sum_sat(lane < kRcWarps ? wt[r * kRcWarps + lane] : 0ull);
+        if (lane == 0) a.ctot[(int64_t)blockIdx.x + (k0 + r) * G] = t;
+      }
+      __syncthreads();  // wt is rewritten by the next batch
     }
   }
   if (bad) record_status(&a.hdr->status, PPL_EINVAL);
@@ -127,7 +231,7 @@ __global__ void __launch_bounds__(kRcTpb, 1) resample_coop_kernel(RcArgs a) {
     const uint64_t wi = warp_scan_u64(run, lane);
     if (lane == 31) jtot[warp] = wi;
     __syncthreads();
-    const uint64_t jv = jtot[lane], ji = warp_scan_u64(jv, lane);
+    const uint64_t jv = lane < kRcWarps ? jtot[lane] : 0ull, ji = warp_scan_u64(jv, lane);
     const uint64_t T = __shfl_sync(0xffffffffu, ji, 31);
     uint64_t cx = sat_add(__shfl_sync(0xffffffffu, ji - jv, warp), wi - run);
     const bool valid = T > 0 && T <= (1ull << 61) && T >= (uint64_t)a.m;
@@ -137,7 +241,11 @@ __global__ void __launch_bounds__(kRcTpb, 1) resample_coop_kernel(RcArgs a) {
       const uint64_t w = philox_block(a.seed, 0, a.instance, a.t, kResample, 0).x;
       u = (__umul64hi(w, stride) << 32) | ((w * stride) >> 32);
     }
-    // exclusive chunk prefixes, first outputs and item counts of this thread's chunks
+    // exclusive chunk prefixes, first outputs and item costs of this thread's
+    // chunks (a chunk with outputs: its items plus kRcPrefixCost)
+    auto cost = [](int64_t k0, int64_t k1) -> int64_t {
+      return k1 > k0 ? (k1 - k0 + kRcItemOut - 1) / kRcItemOut + kRcPrefixCost : 0;
+    };
     int64_t items = 0;
     for (int64_t ch = c0; ch < c1; ++ch) {
       const uint64_t t_ch = __ldcg(a.ctot + ch);
@@ -145,7 +253,7 @@ __global__ void __launch_bounds__(kRcTpb, 1) resample_coop_kernel(RcArgs a) {
       const int64_t k1 = valid ? positions_below(sat_add(cx, t_ch), u, stride, a.m) : 0;
       a.ctot[ch] = cx;
       a.kfirst[ch] = k0;
-      items += (k1 - k0 + kRcItemOut - 1) / kRcItemOut;
+      items += cost(k0, k1);
       cx = sat_add(cx, t_ch);
     }
     // exclusive scan of the item counts
@@ -157,7 +265,7 @@ __global__ void __launch_bounds__(kRcTpb, 1) resample_coop_kernel(RcArgs a) {
     }
     if (lane == 31) jitem[warp] = ii;
     __syncthreads();
-    int64_t iv = jitem[lane], iw = iv;
+    int64_t iv = lane < kRcWarps ? jitem[lane] : 0, iw = iv;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       const int64_t y = __shfl_up_sync(0xffffffffu, iw, o);
@@ -169,7 +277,7 @@ __global__ void __launch_bounds__(kRcTpb, 1) resample_coop_kernel(RcArgs a) {
       a.ioff[ch] = ix;
       const int64_t k0 = __ldcg(a.kfirst + ch);
       const int64_t k1 = ch + 1 < a.n_chunks ? __ldcg(a.kfirst + ch + 1) : a.m;
-      ix += (k1 - k0 + kRcItemOut - 1) / kRcItemOut;
+      ix += cost(k0, k1);
     }
     if (tid == 0) {
       if (T == 0) record_status(&a.hdr->status, PPL_EEMPTY);
@@ -190,94 +298,91 @@ __global__ void __launch_bounds__(kRcTpb, 1) resample_coop_kernel(RcArgs a) {
   const int64_t n_items = (int64_t)(rel & ((1ull << 34) - 1));
   const uint64_t stride = view[1], u = view[2];
 
-  // 3. work items: block b takes the contiguous run [I b / G, I (b + 1) / G),
-  // so consecutive items usually share a chunk, whose prefix sums then stay
-  // in shared memory
-  const int64_t it0 = n_items * blockIdx.x / G, it1 = n_items * (blockIdx.x + 1) / G;
-  int64_t ch_t0 = -1;  // thread 0: chunk of the previous item
-  for (int64_t it = it0; it < it1; ++it) {
-    __syncthreads();  // the previous item has read sO and item_sh
-    if (tid == 0) {
-      int64_t lo = ch_t0 < 0 ? 0 : ch_t0;
-      if (ch_t0 < 0 || __ldcg(a.ioff + ch_t0 + 1) <= it) {
-        int64_t hi = a.n_chunks;  // the last chunk with ioff <= it (ioff[n_chunks] > it)
-        while (hi - lo > 1) {
-          const int64_t mid = (lo + hi) >> 1;
-          if (__ldcg(a.ioff + mid) <= it) lo = mid;
-          else hi = mid;
-        }
-      }
-      const int64_t kc = __ldcg(a.kfirst + lo), kn = __ldcg(a.kfirst + lo + 1);
-      const int64_t first = kc + (it - __ldcg(a.ioff + lo)) * kRcItemOut;
-      item_sh[0] = lo;
-      item_sh[1] = (int64_t)__ldcg(a.ctot + lo);
-      item_sh[2] = first;
-      item_sh[3] = first + kRcItemOut < kn ? first + kRcItemOut : kn;
-      item_sh[4] = lo != ch_t0;  // new chunk: its prefix sums are formed below
-      ch_t0 = lo;
+  // 3. work items: block b takes the contiguous run [I b / G, I (b + 1) / G)
+  // of cost units and walks it chunk by chunk.  Chunk c's units are
+  // [ioff_c, ioff_c+1): kRcPrefixCost that stand for its prefix sums, then one
+  // per item; a run that holds none of the chunk's items skips the chunk.
+  const int64_t it1 = n_items * (blockIdx.x + 1) / G;
+  int32_t* sWw = sW + warp * kRcItemOut;
+  for (int64_t it = n_items * blockIdx.x / G; it < it1;) {
+    if (warp == 0) {  // the chunk of item `it`: the last with ioff <= it
+      // ioff[0] = 0 <= it < ioff[n_chunks] = n_items, so ch lies in [0, n_chunks)
+      int64_t ch = warp_first_above(a.ioff, 0, a.n_chunks + 1, it, lane) - 1;
+      ch = ch < 0 ? 0 : (ch < a.n_chunks ? ch : a.n_chunks - 1);
+      int64_t v = 0;
+      if (lane == 1) v = __ldcg(a.ioff + ch);
+      if (lane == 2) v = __ldcg(a.ioff + ch + 1);
+      if (lane == 3) v = __ldcg(a.kfirst + ch);
+      if (lane == 4) v = __ldcg(a.kfirst + ch + 1);
+      if (lane == 5) v = (int64_t)__ldcg(a.ctot + ch);
+      if (lane == 0) v = ch;
+      if (lane < 6) seg_sh[lane] = v;
     }
     __syncthreads();
-    const int64_t ch = item_sh[0], k0 = item_sh[2], k1 = item_sh[3];
-    const uint64_t cstart = (uint64_t)item_sh[1];
+    const int64_t ch = seg_sh[0], io0 = seg_sh[1], io1 = seg_sh[2] < it1 ? seg_sh[2] : it1;
+    const int64_t kc = seg_sh[3], kn = seg_sh[4];
+    const uint64_t cstart = (uint64_t)seg_sh[5];
     const int64_t cb = ch * kRcChunk;
-    if (item_sh[4]) {  // the same for every thread of the block
-      uint64_t p[kRcItems];
-      load_weights<FROM_LW>(a, cb + (int64_t)tid * kRcItems, m_lw, scale, p, bad);
+    const int64_t xs = it > io0 + kRcPrefixCost ? it : io0 + kRcPrefixCost;  // first item unit
+    if (xs < io1) {  // the same for every thread of the block
+      {  // the chunk's inclusive prefix sums, every 8th and every 256th
+        uint64_t p[kRcItems];
+        load_weights<FROM_LW>(a, cb + (int64_t)tid * kRcItems, m_lw, scale, p, bad);
 #pragma unroll
-      for (int r = 1; r < kRcItems; ++r) p[r] = sat_add(p[r], p[r - 1]);
-      const uint64_t own = p[kRcItems - 1];
-      const uint64_t inc = warp_scan_u64(own, lane);
-      if (lane == 31) wtot[warp] = inc;
-      __syncthreads();
-      const uint64_t v = wtot[lane], wi = warp_scan_u64(v, lane);
-      const uint64_t base = sat_add(cstart, sat_add(__shfl_sync(0xffffffffu, wi - v, warp), inc - own));
+        for (int r = 1; r < kRcItems; ++r) p[r] = sat_add(p[r], p[r - 1]);
+        const uint64_t own = p[kRcItems - 1];
+        const uint64_t inc = warp_scan_u64(own, lane);
+        if (lane == 31) wtot[warp] = inc;
+        __syncthreads();
+        const uint64_t v = lane < kRcWarps ? wtot[lane] : 0ull, wi = warp_scan_u64(v, lane);
+        const uint64_t base = sat_add(cstart, sat_add(__shfl_sync(0xffffffffu, wi - v, warp), inc - own));
 #pragma unroll
-      for (int r = 0; r < kRcItems; ++r) sA[tid * kRcItems + r] = sat_add(base, p[r]);
-      __syncthreads();
-    }
-    {
+        for (int r = 0; r < kRcItems; ++r) sA[tid * kRcItems + r] = sat_add(base, p[r]);
+        const uint64_t last = sat_add(base, own);
+        sL2[tid] = last;
+        if ((tid & 31) == 31) sL1[tid >> 5] = last;  // thread 32 i + 31 ends 256-block i
+        __syncthreads();
+      }
       const int nC = (int)(a.n - cb < kRcChunk ? a.n - cb : kRcChunk);
-      const int nB = (int)(k1 - k0);
-      const uint64_t pos0 = u + (uint64_t)k0 * stride;  // position of output k0
-      const uint64_t posl = pos0 + (uint64_t)(nB - 1) * stride;
-      // only A's between the first above pos0 and the first above the last
-      // position can be ancestors (with degenerate weights, a handful)
-      auto upper = [&](uint64_t v) {
-        int lo = 0, hi = nC;
-        while (lo < hi) {
+      for (int64_t x = xs + warp; x < io1; x += kRcWarps) {
+        const int64_t k0 = kc + (x - io0 - kRcPrefixCost) * kRcItemOut;
+        const int nB = (int)(kn - k0 < kRcItemOut ? kn - k0 : kRcItemOut);
+        const uint64_t pos0 = u + (uint64_t)k0 * stride;  // position of output k0
+        const uint64_t posl = pos0 + (uint64_t)(nB - 1) * stride;
+        // only A's from the first above pos0 to the first above the last
+        // position can be ancestors (with degenerate weights, a handful)
+        const int ia = chunk_first_above(sA, sL2, sL1, pos0, lane);
+        const int ib = min(chunk_first_above(sA, sL2, sL1, posl, lane) + 1, nC);
+        const uint64_t* A = sA + ia;
+        const int nA = ib - ia;
+        const int L = nA + nB;
+        const int d0 = L * lane / 32, d1 = L * (lane + 1) / 32;
+        int lo = d0 > nB ? d0 - nB : 0, hi = d0 < nA ? d0 : nA;
+        while (lo < hi) {  // the prefix sums among the first d0 merged items (ties: A first)
           const int mid = (lo + hi) >> 1;
-          if (sA[mid] <= v) lo = mid + 1;
+          if (A[mid] <= pos0 + (uint64_t)(d0 - 1 - mid) * stride) lo = mid + 1;
           else hi = mid;
         }
-        return lo;
-      };
-      const int ia = upper(pos0), ib = min(upper(posl) + 1, nC);
-      const uint64_t* A = sA + ia;
-      const int nA = ib - ia;
-      const int L = nA + nB;
-      const int d0 = (int)((int64_t)L * tid / kRcTpb), d1 = (int)((int64_t)L * (tid + 1) / kRcTpb);
-      int lo = d0 > nB ? d0 - nB : 0, hi = d0 < nA ? d0 : nA;
-      while (lo < hi) {  // the prefix sums among the first d0 merged items (ties: A first)
-        const int mid = (lo + hi) >> 1;
-        if (A[mid] <= pos0 + (uint64_t)(d0 - 1 - mid) * stride) lo = mid + 1;
-        else hi = mid;
-      }
-      int i = lo, j = d0 - lo;
-      uint64_t bj = pos0 + (uint64_t)j * stride;
-      uint64_t ai = i < nA ? A[i] : ~0ull;
-      for (int s = d0; s < d1; ++s) {
-        if (j >= nB || ai <= bj) {
-          ++i;
-          ai = i < nA ? A[i] : ~0ull;
-        } else {  // output k0 + j: ancestor cb + ia + i (A_i > its position, so i < nA)
-          sO[j] = (int32_t)(cb + ia + (i < nA ? i : nA - 1));
-          ++j;
-          bj += stride;
+        int i = lo, j = d0 - lo;
+        uint64_t bj = pos0 + (uint64_t)j * stride;
+        uint64_t ai = i < nA ? A[i] : ~0ull;
+        for (int s = d0; s < d1; ++s) {
+          if (j >= nB || ai <= bj) {
+            ++i;
+            ai = i < nA ? A[i] : ~0ull;
+          } else {  // output k0 + j: ancestor cb + ia + i (A_i > its position, so i < nA)
+            sWw[j] = (int32_t)(cb + ia + (i < nA ? i : nA - 1));
+            ++j;
+            bj += stride;
+          }
         }
+        __syncwarp();
+        for (int jj = lane; jj < nB; jj += 32) a.anc[k0 + jj] = sWw[jj];
+        __syncwarp();  // sWw is rewritten by the warp's next item
       }
-      __syncthreads();
-      for (int jj = tid; jj < nB; jj += kRcTpb) a.anc[k0 + jj] = sO[jj];
     }
+    __syncthreads();  // sA, its index and seg_sh are rewritten for the next chunk
+    it = io1;
   }
 }
 
@@ -315,7 +420,8 @@ cudaError_t launch_resample_coop(const float* lw, const uint64_t* q_fixed, const
   a.ctot = reinterpret_cast<uint64_t*>(take((size_t)a.n_chunks * 8));
   a.kfirst = reinterpret_cast<int64_t*>(take((size_t)(a.n_chunks + 1) * 8));
   a.ioff = reinterpret_cast<int64_t*>(take((size_t)(a.n_chunks + 1) * 8));
-  constexpr size_t dyn = (size_t)kRcChunk * sizeof(uint64_t) + (size_t)kRcItemOut * sizeof(int32_t);
+  constexpr size_t dyn = (size_t)kRcChunk * sizeof(uint64_t) + (size_t)kRcTpb * sizeof(uint64_t) +
+                         (size_t)kRcWarps * kRcItemOut * sizeof(int32_t);
   const void* fn = lw ? (const void*)resample_coop_kernel<true> : (const void*)resample_coop_kernel<false>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
   if (e != cudaSuccess) return e;

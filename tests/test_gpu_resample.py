@@ -24,7 +24,8 @@ def _t(a):
 
 
 @pytest.mark.parametrize("N,M", [(1, 1), (2, 5), (2047, 2049), (2048, 2048), (2049, 100),
-                                 (100003, 77777), (65536, 300000)])
+                                 (100003, 77777), (65536, 300000), (3, 1 << 20),
+                                 (40000, 1 << 21)])
 def test_fixed_point_ancestors_bit_exact(ppl, orc, N, M):
     q = synth.fixed_weights(N, N + M)
     if q.sum() == 0:
