@@ -253,7 +253,8 @@ ppl_status ppl_resample(const float* lw, const uint64_t* q_fixed, int64_t n, int
 
 /* ppl_resample from lw when the maximum log-weight is already known on the
  * device, e.g. &out_dev->max_lw of the ppl_infer_is that produced lw (whose
- * status was PPL_OK): saves a pass over lw.  NaN log-weights are not detected. */
+ * status was PPL_OK): saves a pass over lw.  NaN log-weights are not detected;
+ * a log-weight above *max_lw_dev is reported as PPL_EINVAL. */
 ppl_status ppl_resample_known_max(const float* lw, const double* max_lw_dev, int64_t n,
                                   int64_t m, uint64_t seed, uint32_t instance, uint32_t t,
                                   int32_t* ancestors, void* ws, size_t ws_bytes,

@@ -99,7 +99,10 @@ __device__ __forceinline__ void to_fixed(const RawWeights<FROM_LW>& w, float m_l
 #pragma unroll
   for (int r = 0; r < kRcItems; ++r) {
     if constexpr (FROM_LW) {
-      q[r] = quantize(w.v[r], m_lw, scale);
+      // a log-weight above the maximum is an error (a wrong known maximum);
+      // otherwise q <= 2^S and no sum of the n weights exceeds 2^61
+      bad |= w.v[r] > m_lw;
+      q[r] = w.v[r] > m_lw ? 0ull : quantize(w.v[r], m_lw, scale);
     } else {
       bad |= w.v[r] > (1ull << 61);
       q[r] = w.v[r] > kLimit ? kLimit : w.v[r];
@@ -115,9 +118,28 @@ __device__ __forceinline__ void load_weights(const RcArgs& a, int64_t base, floa
   to_fixed<FROM_LW>(w, m_lw, scale, q, bad);
 }
 
-__device__ __forceinline__ uint64_t warp_sum_sat(uint64_t v) {
+// Sums of fixed-point weights: plain for quantised log-weights (they cannot
+// pass 2^61, see to_fixed), saturating for given fixed-point words.
+template <bool FROM_LW>
+__device__ __forceinline__ uint64_t acc_add(uint64_t a, uint64_t b) {
+  if constexpr (FROM_LW) return a + b;
+  else return sat_add(a, b);
+}
+
+template <bool FROM_LW>
+__device__ __forceinline__ uint64_t warp_sum_acc(uint64_t v) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = sat_add(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = acc_add<FROM_LW>(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <bool FROM_LW>
+__device__ __forceinline__ uint64_t warp_scan_acc(uint64_t v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v = acc_add<FROM_LW>(v, u);
+  }
   return v;
 }
 
@@ -198,14 +220,14 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
         uint64_t q[kRcItems], t0 = 0, t1 = 0;
         to_fixed<FROM_LW>(w0, m_lw, scale, q, bad);
 #pragma unroll
-        for (int i = 0; i < kRcItems; ++i) t0 = sat_add(t0, q[i]);
+        for (int i = 0; i < kRcItems; ++i) t0 = acc_add<FROM_LW>(t0, q[i]);
         if (r + 1 < nb) {
           to_fixed<FROM_LW>(w1, m_lw, scale, q, bad);
 #pragma unroll
-          for (int i = 0; i < kRcItems; ++i) t1 = sat_add(t1, q[i]);
+          for (int i = 0; i < kRcItems; ++i) t1 = acc_add<FROM_LW>(t1, q[i]);
         }
-        t0 = warp_sum_sat(t0);
-        t1 = warp_sum_sat(t1);
+        t0 = warp_sum_acc<FROM_LW>(t0);
+        t1 = warp_sum_acc<FROM_LW>(t1);
         if (lane == 0) {
           wt[r * kRcWarps + warp] = t0;
           if (r + 1 < nb) wt[(r + 1) * kRcWarps + warp] = t1;
@@ -213,7 +235,7 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
       }
       __syncthreads();
       for (int r = warp; r < nb; r += kRcWarps) {
-        const uint64_t t = warp_sum_sat(lane < kRcWarps ? wt[r * kRcWarps + lane] : 0ull);
+        const uint64_t t = warp_sum_acc<FROM_LW>(lane < kRcWarps ? wt[r * kRcWarps + lane] : 0ull);
         if (lane == 0) a.ctot[(int64_t)blockIdx.x + (k0 + r) * G] = t;
       }
       __syncthreads();  // wt is rewritten by the next batch
@@ -246,15 +268,24 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
     auto cost = [](int64_t k0, int64_t k1) -> int64_t {
       return k1 > k0 ? (k1 - k0 + kRcItemOut - 1) / kRcItemOut + kRcPrefixCost : 0;
     };
+    // (a chunk's last output bound is the next chunk's first: one division
+    // per chunk).  The costs wait in shared memory (sA is unused until phase
+    // 3), or in ioff for more chunks than it holds, for the second pass.
+    int32_t* scost = reinterpret_cast<int32_t*>(sA);
+    const bool cost_smem = a.n_chunks <= 2 * kRcChunk;
     int64_t items = 0;
+    int64_t kprev = (valid && c0 < c1) ? positions_below(cx, u, stride, a.m) : 0;
     for (int64_t ch = c0; ch < c1; ++ch) {
-      const uint64_t t_ch = __ldcg(a.ctot + ch);
-      const int64_t k0 = valid ? positions_below(cx, u, stride, a.m) : 0;
-      const int64_t k1 = valid ? positions_below(sat_add(cx, t_ch), u, stride, a.m) : 0;
+      const uint64_t cn = sat_add(cx, __ldcg(a.ctot + ch));
+      const int64_t knext = valid ? positions_below(cn, u, stride, a.m) : 0;
       a.ctot[ch] = cx;
-      a.kfirst[ch] = k0;
-      items += cost(k0, k1);
-      cx = sat_add(cx, t_ch);
+      a.kfirst[ch] = kprev;
+      const int64_t cc = cost(kprev, knext);  // < 2^31: at most m / 256 + kRcPrefixCost
+      if (cost_smem) scost[ch] = (int32_t)cc;
+      else a.ioff[ch] = cc;
+      items += cc;
+      kprev = knext;
+      cx = cn;
     }
     // exclusive scan of the item counts
     int64_t ii = items;
@@ -273,11 +304,10 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
     }
     int64_t ix = __shfl_sync(0xffffffffu, iw - iv, warp) + (ii - items);
     const int64_t n_items = __shfl_sync(0xffffffffu, iw, 31);
-    for (int64_t ch = c0; ch < c1; ++ch) {  // K of the next chunk: written before the barrier above
+    for (int64_t ch = c0; ch < c1; ++ch) {  // this thread's own costs from the first pass
+      const int64_t cc = cost_smem ? (int64_t)scost[ch] : a.ioff[ch];
       a.ioff[ch] = ix;
-      const int64_t k0 = __ldcg(a.kfirst + ch);
-      const int64_t k1 = ch + 1 < a.n_chunks ? __ldcg(a.kfirst + ch + 1) : a.m;
-      ix += cost(k0, k1);
+      ix += cc;
     }
     if (tid == 0) {
       if (T == 0) record_status(&a.hdr->status, PPL_EEMPTY);
@@ -329,16 +359,18 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
         uint64_t p[kRcItems];
         load_weights<FROM_LW>(a, cb + (int64_t)tid * kRcItems, m_lw, scale, p, bad);
 #pragma unroll
-        for (int r = 1; r < kRcItems; ++r) p[r] = sat_add(p[r], p[r - 1]);
+        for (int r = 1; r < kRcItems; ++r) p[r] = acc_add<FROM_LW>(p[r], p[r - 1]);
         const uint64_t own = p[kRcItems - 1];
-        const uint64_t inc = warp_scan_u64(own, lane);
+        const uint64_t inc = warp_scan_acc<FROM_LW>(own, lane);
         if (lane == 31) wtot[warp] = inc;
         __syncthreads();
-        const uint64_t v = lane < kRcWarps ? wtot[lane] : 0ull, wi = warp_scan_u64(v, lane);
-        const uint64_t base = sat_add(cstart, sat_add(__shfl_sync(0xffffffffu, wi - v, warp), inc - own));
+        const uint64_t v = lane < kRcWarps ? wtot[lane] : 0ull;
+        const uint64_t wi = warp_scan_acc<FROM_LW>(v, lane);
+        const uint64_t base = acc_add<FROM_LW>(
+            cstart, acc_add<FROM_LW>(__shfl_sync(0xffffffffu, wi - v, warp), inc - own));
 #pragma unroll
-        for (int r = 0; r < kRcItems; ++r) sA[tid * kRcItems + r] = sat_add(base, p[r]);
-        const uint64_t last = sat_add(base, own);
+        for (int r = 0; r < kRcItems; ++r) sA[tid * kRcItems + r] = acc_add<FROM_LW>(base, p[r]);
+        const uint64_t last = acc_add<FROM_LW>(base, own);
         sL2[tid] = last;
         if ((tid & 31) == 31) sL1[tid >> 5] = last;  // thread 32 i + 31 ends 256-block i
         __syncthreads();
@@ -355,6 +387,11 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
         const int ib = min(chunk_first_above(sA, sL2, sL1, posl, lane) + 1, nC);
         const uint64_t* A = sA + ia;
         const int nA = ib - ia;
+        if (nA == 1) {  // one ancestor for the whole item (degenerate weights)
+          const int32_t an = (int32_t)(cb + ia);
+          for (int jj = lane; jj < nB; jj += 32) a.anc[k0 + jj] = an;
+          continue;
+        }
         const int L = nA + nB;
         const int d0 = L * lane / 32, d1 = L * (lane + 1) / 32;
         int lo = d0 > nB ? d0 - nB : 0, hi = d0 < nA ? d0 : nA;

@@ -96,6 +96,18 @@ def test_device_errors_are_reported(ppl):
     torch.cuda.synchronize()
 
 
+def test_known_max_below_a_log_weight_is_reported(ppl):
+    import torch
+    lw = synth.log_weights(10000, 5, "normal")
+    ws = ppl.workspace(ppl.poly_model(), 10000)
+    mx = torch.tensor([float(lw.max()) - 1.0], dtype=torch.float64, device="cuda")
+    ppl.ppl_resample_known_max(10000, 1, _t(lw), mx, ws=ws)
+    assert ppl.ppl_workspace_status(ws) == ppl.PPL_EINVAL
+    mx = torch.tensor([float(lw.max())], dtype=torch.float64, device="cuda")
+    ppl.ppl_resample_known_max(10000, 1, _t(lw), mx, ws=ws)
+    assert ppl.ppl_workspace_status(ws) == ppl.PPL_OK
+
+
 def test_known_max_matches_plain_resample(ppl, orc):
     import torch
     x, y = synth.poly_dataset(64, 2)
