@@ -70,7 +70,7 @@ __device__ __forceinline__ void finalize_partials(const DegPartial* parts, int G
 // last block merges the blocks' partials into the summary.
 // ---------------------------------------------------------------------------
 template <int PPT>
-__global__ void __launch_bounds__(kTpb, 3) poly_trace_kernel(
+__global__ void __launch_bounds__(kTpb, 4) poly_trace_kernel(
     PolyParams p, const float* __restrict__ xs, const float* __restrict__ ys, int64_t L,
     int64_t N, uint64_t seed, uint32_t instance, int chunk, float* __restrict__ lw_out,
     ppl_poly_particle* __restrict__ rec_out, WsHeader* hdr, DegPartial* parts,
@@ -101,6 +101,15 @@ __global__ void __launch_bounds__(kTpb, 3) poly_trace_kernel(
     trace_group<PPT>(PriorDraw{p, seed, instance}, p, xs, ys, L, chunk, resident, sdata, N,
                      g * group, lw_out, rec_out, ts, suff);
     if (tid == 0) nan |= ts.nan;
+    // the block's running per-degree maxima bound the final maxima from
+    // below, so later groups skip traces far beneath them (taken at the group
+    // boundary, after trace_group's closing barrier: deterministic)
+    if (tid < kMaxDegrees) {
+      float m = ts.ext_max[tid];
+#pragma unroll
+      for (int w = 0; w < kTpb / 32; ++w) m = fmaxf(m, ts.wrun[w * kMaxDegrees + tid].m);
+      ts.ext_max[tid] = m;
+    }
   }
   merge_warp_partials(ts, run);
   if (tid < kMaxDegrees) parts[blockIdx.x * kMaxDegrees + tid] = run[tid];
