@@ -22,8 +22,9 @@ WsLayout layout(int64_t n, int64_t data_len) {
   size_t off = 0;
   w.header = off;
   off += kHeaderBytes;
-  w.tiles = off;
-  off += align_up((size_t)scan_tiles(std::max<int64_t>(n, 1)) * sizeof(uint64_t));
+  w.tiles = off;  // scan tile status words, or the cooperative resampler's barrier words
+  off += align_up(std::max((size_t)scan_tiles(std::max<int64_t>(n, 1)) * sizeof(uint64_t),
+                           resample_coop_barrier_bytes()));
   w.partials = off;
   off += align_up(partials_bytes());
   w.prefix = off;  // prefix sums C, or the cooperative resampler's tables
@@ -301,10 +302,11 @@ static ppl_status resample_impl(const float* lw, const uint64_t* q_fixed, const 
   PPL_TRY(reset_ws(w, true, s));
   if (lw && !known_max)
     PPL_TRY(cuda_status(launch_stats(lw, n, w.hdr(), w.partials(), nullptr, s)));
-  // the prefix-sum region holds the resampling kernel's barrier words and
-  // per-chunk tables (a few bytes per 8192 particles)
+  // the scan-tile region (cleared with the header above) holds the
+  // resampling kernel's barrier words, the prefix-sum region its per-chunk
+  // tables (a few bytes per 4096 particles)
   PPL_TRY(cuda_status(launch_resample_coop(lw, q_fixed, known_max, n, m, seed, instance, t,
-                                           w.hdr(), reinterpret_cast<char*>(w.prefix()),
+                                           w.hdr(), w.tiles(), reinterpret_cast<char*>(w.prefix()),
                                            w.l.bounds - w.l.prefix, ancestors, nullptr, s)));
   return PPL_OK;
 }
@@ -371,7 +373,7 @@ ppl_status ppl_smc_step(const ppl_model* model, float y_t, int32_t t, uint64_t s
   PPL_TRY(cuda_status(launch_smc_propagate(p, y_t, t, seed, x, lw, n, logz_acc, resampled,
                                            logz_est, w.hdr(), w.partials(), s)));
   PPL_TRY(cuda_status(launch_resample_coop(lw, nullptr, nullptr, n, n, seed, 0, (uint32_t)t,
-                                           w.hdr(), reinterpret_cast<char*>(w.prefix()),
+                                           w.hdr(), w.tiles(), reinterpret_cast<char*>(w.prefix()),
                                            w.l.bounds - w.l.prefix, anc, gate, s)));
   PPL_TRY(cuda_status(launch_gather(x, n, sizeof(float), anc, n, x_tmp, gate, s)));
   PPL_TRY(cuda_status(launch_smc_commit(x, x_tmp, lw, n, gate, s)));

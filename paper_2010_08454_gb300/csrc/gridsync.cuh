@@ -140,4 +140,29 @@ __device__ __forceinline__ int64_t positions_below(uint64_t c, uint64_t u, uint6
   return k < (uint64_t)m ? (int64_t)k : m;
 }
 
+// Division by an invariant divisor d (Granlund and Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994): with
+// inv = floor((2^64 - 1) / d), the high word of num * inv never exceeds
+// floor(num / d) and, for num < 2^62, falls short of it by at most one, which
+// one remainder test corrects.
+struct DivInv {
+  uint64_t d, inv;
+};
+__device__ __forceinline__ DivInv div_inv(uint64_t d) { return DivInv{d, d ? ~0ull / d : 0ull}; }
+__device__ __forceinline__ uint64_t div_by(uint64_t num, const DivInv& v) {
+  uint64_t q = __umul64hi(num, v.inv);
+  const uint64_t r = num - q * v.d;  // < 2 d
+  if (r >= v.d) ++q;
+  return q;
+}
+
+// positions_below with the stride's reciprocal precomputed (num < 2^62 holds:
+// c <= 2^61 and stride <= 2^61).
+__device__ __forceinline__ int64_t positions_below_inv(uint64_t c, uint64_t u, const DivInv& sv,
+                                                       int64_t m) {
+  if (c <= u) return 0;
+  const uint64_t k = div_by(c - u + sv.d - 1, sv);
+  return k < (uint64_t)m ? (int64_t)k : m;
+}
+
 }  // namespace ppl

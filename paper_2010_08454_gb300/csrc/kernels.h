@@ -83,13 +83,15 @@ cudaError_t launch_smc_propagate(const LgssmParams& p, float y_t, int32_t t, uin
                                  int32_t* resampled, double* logz_est, WsHeader* hdr,
                                  void* parts, cudaStream_t s);
 size_t smc_run_workspace(int64_t N, int64_t T);
-// Systematic resampling in one cooperative kernel (ancestors only); `scratch`
-// holds the barrier words and the per-chunk tables (resample_coop_scratch(n)
-// bytes, 128-byte aligned).
+// Systematic resampling in one cooperative kernel (ancestors only).
+// `barrier` holds the grid barrier's words (resample_coop_barrier_bytes(),
+// 128-byte aligned, zeroed by the caller before the launch); `scratch` the
+// per-chunk tables (resample_coop_scratch(n) bytes, 16-byte aligned).
 size_t resample_coop_scratch(int64_t n);
+size_t resample_coop_barrier_bytes();
 cudaError_t launch_resample_coop(const float* lw, const uint64_t* q_fixed, const double* known_max,
                                  int64_t n, int64_t m, uint64_t seed, uint32_t instance, uint32_t t,
-                                 WsHeader* hdr, char* scratch, size_t scratch_bytes,
+                                 WsHeader* hdr, void* barrier, char* scratch, size_t scratch_bytes,
                                  int32_t* anc, const int32_t* gate, cudaStream_t s);
 cudaError_t launch_smc_persistent(const LgssmParams& p, const float* y, int32_t T, uint64_t seed,
                                   int64_t N, float* x_out, float* lw_out, double* logz,

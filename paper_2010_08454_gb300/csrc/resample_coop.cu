@@ -44,6 +44,7 @@ constexpr int kRcBatch = 32;                          // chunks summed between b
 // items over the blocks, so that a block whose run crosses many sparsely
 // used chunks takes correspondingly fewer items.
 constexpr int kRcPrefixCost = 64;
+constexpr int kRcJobBlk = 8;  // chunk totals the layout job loads at once per thread
 
 struct RcArgs {
   const float* lw;         // FP32 log-weights, or
@@ -93,17 +94,30 @@ __device__ __forceinline__ void load_raw(const RcArgs& a, int64_t base, RawWeigh
 }
 
 // Fixed-point weights from raw ones (log-weights quantised against m_lw).
+// A log-weight more than 44.5 below the maximum quantises to 0; when that
+// holds for all of a warp's weights (most of them, for degenerate importance
+// weights) the exponentials are skipped.
 template <bool FROM_LW>
 __device__ __forceinline__ void to_fixed(const RawWeights<FROM_LW>& w, float m_lw, float scale,
                                          uint64_t (&q)[kRcItems], int& bad) {
+  if constexpr (FROM_LW) {
+    bool near = false;
 #pragma unroll
-  for (int r = 0; r < kRcItems; ++r) {
-    if constexpr (FROM_LW) {
+    for (int r = 0; r < kRcItems; ++r) {
       // a log-weight above the maximum is an error (a wrong known maximum);
       // otherwise q <= 2^S and no sum of the n weights exceeds 2^61
       bad |= w.v[r] > m_lw;
-      q[r] = w.v[r] > m_lw ? 0ull : quantize(w.v[r], m_lw, scale);
-    } else {
+      near |= __fsub_rn(w.v[r], m_lw) >= -44.5f;
+      q[r] = 0ull;
+    }
+    if (__any_sync(0xffffffffu, near)) {
+#pragma unroll
+      for (int r = 0; r < kRcItems; ++r)
+        q[r] = w.v[r] > m_lw ? 0ull : quantize(w.v[r], m_lw, scale);
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < kRcItems; ++r) {
       bad |= w.v[r] > (1ull << 61);
       q[r] = w.v[r] > kLimit ? kLimit : w.v[r];
     }
@@ -178,6 +192,31 @@ __device__ __forceinline__ int chunk_first_above(const uint64_t* sA, const uint6
   return t + (m ? __ffs(m) - 1 : 7);
 }
 
+// Descriptor of the chunk that holds cost unit `it` (the last chunk with
+// ioff <= it), by one warp: chunk, ioff of it and of the next, first output
+// of it and of the next, and its prefix start.  With a hint (a chunk whose
+// ioff is it) the warp first probes the 32 chunks from the hint at once, so
+// the next chunk of a run costs one round trip; otherwise, or when all 32 lie
+// at or below it, a 32-way search.  ioff[0] = 0 <= it < ioff[n_chunks].
+__device__ __forceinline__ void seg_lookup(const RcArgs& a, int64_t it, int64_t hint, int64_t* out,
+                                           int lane) {
+  int64_t ch = -1;
+  if (hint >= 0) {
+    const int64_t q = hint + lane;
+    const unsigned m = __ballot_sync(0xffffffffu, q <= a.n_chunks && __ldcg(a.ioff + q) <= it);
+    if (m != 0xffffffffu) ch = hint + __popc(m) - 1;  // ioff is non-decreasing: m is a prefix
+  }
+  if (ch < 0) ch = warp_first_above(a.ioff, hint > 0 ? hint : 0, a.n_chunks + 1, it, lane) - 1;
+  ch = ch < 0 ? 0 : (ch < a.n_chunks ? ch : a.n_chunks - 1);
+  int64_t v = ch;
+  if (lane == 1) v = __ldcg(a.ioff + ch);
+  if (lane == 2) v = __ldcg(a.ioff + ch + 1);
+  if (lane == 3) v = __ldcg(a.kfirst + ch);
+  if (lane == 4) v = __ldcg(a.kfirst + ch + 1);
+  if (lane == 5) v = (int64_t)__ldcg(a.ctot + ch);
+  if (lane < 6) out[lane] = v;
+}
+
 template <bool FROM_LW>
 __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
   if (a.gate && *a.gate == 0) return;  // every block reads the same flag
@@ -190,7 +229,7 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
   __shared__ int64_t jitem[kRcWarps];
   __shared__ unsigned long long rel;
   __shared__ uint64_t view[3];  // T, stride, u
-  __shared__ int64_t seg_sh[6];  // chunk, its first item, end item, first and end output, C at its start
+  __shared__ int64_t seg_sh[2][6];  // chunk, its first and end unit, first and end output, C at its start
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned G = gridDim.x;
   float m_lw = 0.0f, scale = 0.0f;
@@ -212,25 +251,25 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
                            ? (a.n_chunks - (int64_t)blockIdx.x + G - 1) / G : 0;
     for (int64_t k0 = 0; k0 < nk; k0 += kRcBatch) {
       const int nb = (int)(nk - k0 < kRcBatch ? nk - k0 : kRcBatch);
-      for (int r = 0; r < nb; r += 2) {
-        const int64_t c0 = (int64_t)blockIdx.x + (k0 + r) * G;
-        RawWeights<FROM_LW> w0, w1;
-        load_raw<FROM_LW>(a, c0 * kRcChunk + (int64_t)tid * kRcItems, w0);
-        if (r + 1 < nb) load_raw<FROM_LW>(a, (c0 + G) * kRcChunk + (int64_t)tid * kRcItems, w1);
-        uint64_t q[kRcItems], t0 = 0, t1 = 0;
-        to_fixed<FROM_LW>(w0, m_lw, scale, q, bad);
+      // kP1 chunks' loads in flight per thread (two for 64-bit input words)
+      constexpr int kP1 = FROM_LW ? 4 : 2;
+      static_assert(kRcBatch % kP1 == 0, "whole rounds per batch");
+      for (int r = 0; r < nb; r += kP1) {
+        RawWeights<FROM_LW> w[kP1];
 #pragma unroll
-        for (int i = 0; i < kRcItems; ++i) t0 = acc_add<FROM_LW>(t0, q[i]);
-        if (r + 1 < nb) {
-          to_fixed<FROM_LW>(w1, m_lw, scale, q, bad);
+        for (int i = 0; i < kP1; ++i)
+          if (r + i < nb)
+            load_raw<FROM_LW>(a, ((int64_t)blockIdx.x + (k0 + r + i) * G) * kRcChunk +
+                                     (int64_t)tid * kRcItems, w[i]);
 #pragma unroll
-          for (int i = 0; i < kRcItems; ++i) t1 = acc_add<FROM_LW>(t1, q[i]);
-        }
-        t0 = warp_sum_acc<FROM_LW>(t0);
-        t1 = warp_sum_acc<FROM_LW>(t1);
-        if (lane == 0) {
-          wt[r * kRcWarps + warp] = t0;
-          if (r + 1 < nb) wt[(r + 1) * kRcWarps + warp] = t1;
+        for (int i = 0; i < kP1; ++i) {
+          if (r + i >= nb) break;  // the same for the whole block
+          uint64_t q[kRcItems], t = 0;
+          to_fixed<FROM_LW>(w[i], m_lw, scale, q, bad);
+#pragma unroll
+          for (int e = 0; e < kRcItems; ++e) t = acc_add<FROM_LW>(t, q[e]);
+          t = warp_sum_acc<FROM_LW>(t);
+          if (lane == 0) wt[(r + i) * kRcWarps + warp] = t;
         }
       }
       __syncthreads();
@@ -248,8 +287,15 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
     // thread tid takes chunks [c0, c1) in order
     const int64_t per = (a.n_chunks + kRcTpb - 1) / kRcTpb;
     const int64_t c0 = (int64_t)tid * per, c1 = c0 + per < a.n_chunks ? c0 + per : a.n_chunks;
+    // (kRcJobBlk of them loaded at once: one L2 round trip, not one each)
     uint64_t run = 0;
-    for (int64_t ch = c0; ch < c1; ++ch) run = sat_add(run, __ldcg(a.ctot + ch));
+    for (int64_t b0 = c0; b0 < c1; b0 += kRcJobBlk) {
+      uint64_t t[kRcJobBlk];
+#pragma unroll
+      for (int r = 0; r < kRcJobBlk; ++r) t[r] = b0 + r < c1 ? __ldcg(a.ctot + b0 + r) : 0ull;
+#pragma unroll
+      for (int r = 0; r < kRcJobBlk; ++r) run = sat_add(run, t[r]);
+    }
     const uint64_t wi = warp_scan_u64(run, lane);
     if (lane == 31) jtot[warp] = wi;
     __syncthreads();
@@ -274,18 +320,31 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
     int32_t* scost = reinterpret_cast<int32_t*>(sA);
     const bool cost_smem = a.n_chunks <= 2 * kRcChunk;
     int64_t items = 0;
-    int64_t kprev = (valid && c0 < c1) ? positions_below(cx, u, stride, a.m) : 0;
-    for (int64_t ch = c0; ch < c1; ++ch) {
-      const uint64_t cn = sat_add(cx, __ldcg(a.ctot + ch));
-      const int64_t knext = valid ? positions_below(cn, u, stride, a.m) : 0;
-      a.ctot[ch] = cx;
-      a.kfirst[ch] = kprev;
-      const int64_t cc = cost(kprev, knext);  // < 2^31: at most m / 256 + kRcPrefixCost
-      if (cost_smem) scost[ch] = (int32_t)cc;
-      else a.ioff[ch] = cc;
-      items += cc;
-      kprev = knext;
-      cx = cn;
+    const DivInv sv = div_inv(stride);
+    int64_t kprev = (valid && c0 < c1) ? positions_below_inv(cx, u, sv, a.m) : 0;
+    for (int64_t b0 = c0; b0 < c1; b0 += kRcJobBlk) {
+      uint64_t cs[kRcJobBlk + 1];  // the prefix at each chunk's start, then past the last
+      cs[0] = cx;
+#pragma unroll
+      for (int r = 0; r < kRcJobBlk; ++r)
+        cs[r + 1] = sat_add(cs[r], b0 + r < c1 ? __ldcg(a.ctot + b0 + r) : 0ull);
+      int64_t kn[kRcJobBlk];  // independent divisions
+#pragma unroll
+      for (int r = 0; r < kRcJobBlk; ++r)
+        kn[r] = (valid && b0 + r < c1) ? positions_below_inv(cs[r + 1], u, sv, a.m) : 0;
+#pragma unroll
+      for (int r = 0; r < kRcJobBlk; ++r) {
+        if (b0 + r >= c1) break;
+        const int64_t ch = b0 + r;
+        a.ctot[ch] = cs[r];
+        a.kfirst[ch] = kprev;
+        const int64_t cc = cost(kprev, kn[r]);  // < 2^31: at most m / 256 + kRcPrefixCost
+        if (cost_smem) scost[ch] = (int32_t)cc;
+        else a.ioff[ch] = cc;
+        items += cc;
+        kprev = kn[r];
+        cx = cs[r + 1];
+      }
     }
     // exclusive scan of the item counts
     int64_t ii = items;
@@ -334,49 +393,45 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
   // per item; a run that holds none of the chunk's items skips the chunk.
   const int64_t it1 = n_items * (blockIdx.x + 1) / G;
   int32_t* sWw = sW + warp * kRcItemOut;
-  for (int64_t it = n_items * blockIdx.x / G; it < it1;) {
-    if (warp == 0) {  // the chunk of item `it`: the last with ioff <= it
-      // ioff[0] = 0 <= it < ioff[n_chunks] = n_items, so ch lies in [0, n_chunks)
-      int64_t ch = warp_first_above(a.ioff, 0, a.n_chunks + 1, it, lane) - 1;
-      ch = ch < 0 ? 0 : (ch < a.n_chunks ? ch : a.n_chunks - 1);
-      int64_t v = 0;
-      if (lane == 1) v = __ldcg(a.ioff + ch);
-      if (lane == 2) v = __ldcg(a.ioff + ch + 1);
-      if (lane == 3) v = __ldcg(a.kfirst + ch);
-      if (lane == 4) v = __ldcg(a.kfirst + ch + 1);
-      if (lane == 5) v = (int64_t)__ldcg(a.ctot + ch);
-      if (lane == 0) v = ch;
-      if (lane < 6) seg_sh[lane] = v;
-    }
-    __syncthreads();
-    const int64_t ch = seg_sh[0], io0 = seg_sh[1], io1 = seg_sh[2] < it1 ? seg_sh[2] : it1;
-    const int64_t kc = seg_sh[3], kn = seg_sh[4];
-    const uint64_t cstart = (uint64_t)seg_sh[5];
+  int64_t it = n_items * blockIdx.x / G;
+  if (warp == 0 && it < it1) seg_lookup(a, it, -1, seg_sh[0], lane);
+  __syncthreads();
+  for (int cur = 0; it < it1; cur ^= 1) {
+    const int64_t ch = seg_sh[cur][0], io0 = seg_sh[cur][1];
+    const int64_t io1 = seg_sh[cur][2] < it1 ? seg_sh[cur][2] : it1;
+    const int64_t kc = seg_sh[cur][3], kn = seg_sh[cur][4];
+    const uint64_t cstart = (uint64_t)seg_sh[cur][5];
+    const bool more = io1 < it1;  // another chunk follows in this block's run
     const int64_t cb = ch * kRcChunk;
     const int64_t xs = it > io0 + kRcPrefixCost ? it : io0 + kRcPrefixCost;  // first item unit
-    if (xs < io1) {  // the same for every thread of the block
-      {  // the chunk's inclusive prefix sums, every 8th and every 256th
-        uint64_t p[kRcItems];
-        load_weights<FROM_LW>(a, cb + (int64_t)tid * kRcItems, m_lw, scale, p, bad);
+    if (xs < io1) {  // the same for every thread of the block: the chunk's inclusive
+      // prefix sums, every 8th and every 256th
+      uint64_t p[kRcItems];
+      load_weights<FROM_LW>(a, cb + (int64_t)tid * kRcItems, m_lw, scale, p, bad);
 #pragma unroll
-        for (int r = 1; r < kRcItems; ++r) p[r] = acc_add<FROM_LW>(p[r], p[r - 1]);
-        const uint64_t own = p[kRcItems - 1];
-        const uint64_t inc = warp_scan_acc<FROM_LW>(own, lane);
-        if (lane == 31) wtot[warp] = inc;
-        __syncthreads();
-        const uint64_t v = lane < kRcWarps ? wtot[lane] : 0ull;
-        const uint64_t wi = warp_scan_acc<FROM_LW>(v, lane);
-        const uint64_t base = acc_add<FROM_LW>(
-            cstart, acc_add<FROM_LW>(__shfl_sync(0xffffffffu, wi - v, warp), inc - own));
+      for (int r = 1; r < kRcItems; ++r) p[r] = acc_add<FROM_LW>(p[r], p[r - 1]);
+      const uint64_t own = p[kRcItems - 1];
+      const uint64_t inc = warp_scan_acc<FROM_LW>(own, lane);
+      if (lane == 31) wtot[warp] = inc;
+      __syncthreads();
+      const uint64_t v = lane < kRcWarps ? wtot[lane] : 0ull;
+      const uint64_t wi = warp_scan_acc<FROM_LW>(v, lane);
+      const uint64_t base = acc_add<FROM_LW>(
+          cstart, acc_add<FROM_LW>(__shfl_sync(0xffffffffu, wi - v, warp), inc - own));
 #pragma unroll
-        for (int r = 0; r < kRcItems; ++r) sA[tid * kRcItems + r] = acc_add<FROM_LW>(base, p[r]);
-        const uint64_t last = acc_add<FROM_LW>(base, own);
-        sL2[tid] = last;
-        if ((tid & 31) == 31) sL1[tid >> 5] = last;  // thread 32 i + 31 ends 256-block i
-        __syncthreads();
-      }
+      for (int r = 0; r < kRcItems; ++r) sA[tid * kRcItems + r] = acc_add<FROM_LW>(base, p[r]);
+      const uint64_t last = acc_add<FROM_LW>(base, own);
+      sL2[tid] = last;
+      if ((tid & 31) == 31) sL1[tid >> 5] = last;  // thread 32 i + 31 ends 256-block i
+      __syncthreads();
+    }
+    // warp 0 fetches the next chunk's descriptor while the others take this
+    // chunk's items
+    if (more && warp == 0) seg_lookup(a, io1, ch + 1, seg_sh[cur ^ 1], lane);
+    if (xs < io1 && !(more && warp == 0)) {
       const int nC = (int)(a.n - cb < kRcChunk ? a.n - cb : kRcChunk);
-      for (int64_t x = xs + warp; x < io1; x += kRcWarps) {
+      const int w0 = more ? 1 : 0, nw = kRcWarps - w0;
+      for (int64_t x = xs + (warp - w0); x < io1; x += nw) {
         const int64_t k0 = kc + (x - io0 - kRcPrefixCost) * kRcItemOut;
         const int nB = (int)(kn - k0 < kRcItemOut ? kn - k0 : kRcItemOut);
         const uint64_t pos0 = u + (uint64_t)k0 * stride;  // position of output k0
@@ -384,14 +439,14 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
         // only A's from the first above pos0 to the first above the last
         // position can be ancestors (with degenerate weights, a handful)
         const int ia = chunk_first_above(sA, sL2, sL1, pos0, lane);
-        const int ib = min(chunk_first_above(sA, sL2, sL1, posl, lane) + 1, nC);
-        const uint64_t* A = sA + ia;
-        const int nA = ib - ia;
-        if (nA == 1) {  // one ancestor for the whole item (degenerate weights)
+        if (posl < sA[ia]) {  // one ancestor for the whole item (degenerate weights)
           const int32_t an = (int32_t)(cb + ia);
           for (int jj = lane; jj < nB; jj += 32) a.anc[k0 + jj] = an;
           continue;
         }
+        const int ib = min(chunk_first_above(sA, sL2, sL1, posl, lane) + 1, nC);
+        const uint64_t* A = sA + ia;
+        const int nA = ib - ia;
         const int L = nA + nB;
         const int d0 = L * lane / 32, d1 = L * (lane + 1) / 32;
         int lo = d0 > nB ? d0 - nB : 0, hi = d0 < nA ? d0 : nA;
@@ -425,14 +480,17 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
 
 size_t resample_coop_scratch(int64_t n) {
   const int64_t chunks = (n + kRcChunk - 1) / kRcChunk;
-  return sizeof(GridCtl) + (size_t)chunks * 8 + 2 * (size_t)(chunks + 1) * 8 + 3 * 16;
+  return (size_t)chunks * 8 + 2 * (size_t)(chunks + 1) * 8 + 2 * 16;
 }
+
+size_t resample_coop_barrier_bytes() { return sizeof(GridCtl); }
 
 cudaError_t launch_resample_coop(const float* lw, const uint64_t* q_fixed, const double* known_max,
                                  int64_t n, int64_t m, uint64_t seed, uint32_t instance, uint32_t t,
-                                 WsHeader* hdr, char* scratch, size_t scratch_bytes,
+                                 WsHeader* hdr, void* barrier, char* scratch, size_t scratch_bytes,
                                  int32_t* anc, const int32_t* gate, cudaStream_t s) {
-  if (scratch_bytes < resample_coop_scratch(n) || (reinterpret_cast<uintptr_t>(scratch) & 127))
+  if (scratch_bytes < resample_coop_scratch(n) || (reinterpret_cast<uintptr_t>(scratch) & 15) ||
+      (reinterpret_cast<uintptr_t>(barrier) & 127))
     return cudaErrorInvalidValue;
   RcArgs a;
   a.lw = lw;
@@ -453,21 +511,24 @@ cudaError_t launch_resample_coop(const float* lw, const uint64_t* q_fixed, const
     off += (bytes + 15) / 16 * 16;
     return q;
   };
-  a.g = reinterpret_cast<GridCtl*>(take(sizeof(GridCtl)));
+  a.g = reinterpret_cast<GridCtl*>(barrier);
   a.ctot = reinterpret_cast<uint64_t*>(take((size_t)a.n_chunks * 8));
   a.kfirst = reinterpret_cast<int64_t*>(take((size_t)(a.n_chunks + 1) * 8));
   a.ioff = reinterpret_cast<int64_t*>(take((size_t)(a.n_chunks + 1) * 8));
   constexpr size_t dyn = (size_t)kRcChunk * sizeof(uint64_t) + (size_t)kRcTpb * sizeof(uint64_t) +
                          (size_t)kRcWarps * kRcItemOut * sizeof(int32_t);
   const void* fn = lw ? (const void*)resample_coop_kernel<true> : (const void*)resample_coop_kernel<false>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-  if (e != cudaSuccess) return e;
-  int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kRcTpb, dyn);
-  if (e != cudaSuccess) return e;
-  const int64_t grid = (int64_t)num_sms() * std::max(per_sm, 1);
-  e = cudaMemsetAsync(a.g, 0, sizeof(GridCtl), s);
-  if (e != cudaSuccess) return e;
+  static int per_sm_of[2] = {0, 0};  // set up once per kernel: attribute and residency
+  int& per_sm = per_sm_of[lw ? 1 : 0];
+  if (per_sm == 0) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+    int r = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, fn, kRcTpb, dyn);
+    if (e != cudaSuccess) return e;
+    per_sm = r > 0 ? r : 1;
+  }
+  const int64_t grid = (int64_t)num_sms() * per_sm;
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kRcTpb), args, dyn, s);
 }
