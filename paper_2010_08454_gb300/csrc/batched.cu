@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(kTpb, PPT >= 8 ? 2 : 3) batched_kernel(
     PolyParams p, const float* __restrict__ xs, const float* __restrict__ ys,
     const int64_t* __restrict__ data_off, const int64_t* __restrict__ part_off,
     const BatchItem* __restrict__ items, int64_t n_items, const int32_t* __restrict__ first,
-    int32_t* count, uint64_t seed, const float* __restrict__ proposal, int* inst_max,
+    int32_t* count, uint64_t seed, const float* __restrict__ proposal, unsigned* inst_max,
     WsHeader* hdr, DegPartial* parts, ppl_is_result* out) {
   extern __shared__ __align__(16) unsigned char smem[];
   TraceSmem<PPT>& ts = *reinterpret_cast<TraceSmem<PPT>*>(smem);
@@ -102,7 +102,8 @@ __global__ void __launch_bounds__(kTpb, PPT >= 8 ? 2 : 3) batched_kernel(
     // maxima already reached by this instance's finished items bound the final
     // maxima from below: traces far beneath them are skipped (trace_group)
     if (tid < kMaxDegrees) {
-      const int k = ld_volatile_i32(inst_max + (int64_t)b * kMaxDegrees + tid);
+      const unsigned k = (unsigned)ld_volatile_i32(reinterpret_cast<const int32_t*>(inst_max) +
+                                                   (int64_t)b * kMaxDegrees + tid);
       ts.ext_max[tid] = (k == 0) ? -INFINITY : key_float(k);
     }
     __syncthreads();
@@ -225,7 +226,7 @@ static cudaError_t launch_batched_t(const PolyParams& p, const float* x, const f
   batched_kernel<PPT, LEARNED><<<(unsigned)grid, kTpb, smem, s>>>(
       p, x, y, data_off, part_off, reinterpret_cast<const BatchItem*>(ws + l.items), n_items,
       reinterpret_cast<const int32_t*>(ws + l.first), reinterpret_cast<int32_t*>(ws + l.count),
-      seed, proposal, reinterpret_cast<int*>(ws + l.inst_max), hdr,
+      seed, proposal, reinterpret_cast<unsigned*>(ws + l.inst_max), hdr,
       reinterpret_cast<DegPartial*>(ws + l.parts), out);
   return cudaGetLastError();
 }

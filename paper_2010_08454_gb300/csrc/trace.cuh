@@ -37,13 +37,14 @@ struct TraceSmem {
   float ext_max[kMaxDegrees];  // known lower bounds of the final per-degree maxima (or -inf)
 };
 
-// Float <-> int keys that order like the floats (for atomicMax on maxima).
-__device__ __forceinline__ int float_key(float f) {
-  const int b = __float_as_int(f);
-  return b >= 0 ? b : (b ^ 0x7fffffff);
+// Float <-> unsigned keys that order like the floats, with key 0 below every
+// float (so a zeroed word means "no maximum yet" and atomicMax on it works).
+__device__ __forceinline__ unsigned float_key(float f) {
+  const unsigned b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
-__device__ __forceinline__ float key_float(int k) {
-  return __int_as_float(k >= 0 ? k : (k ^ 0x7fffffff));
+__device__ __forceinline__ float key_float(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
 }
 
 // Clear the warps' running partials (before the first group).
