@@ -44,7 +44,9 @@ constexpr int kRcBatch = 32;                          // chunks summed between b
 // items over the blocks, so that a block whose run crosses many sparsely
 // used chunks takes correspondingly fewer items.
 constexpr int kRcPrefixCost = 64;
-constexpr int kRcJobBlk = 8;  // chunk totals the layout job loads at once per thread
+constexpr int kRcJobBlk = 8;     // chunk totals the layout job's first pass loads at once per thread
+constexpr int kRcJobPer = 4;     // chunks per thread in a tile of the layout job
+constexpr int kRcJobTile = kRcTpb * kRcJobPer;
 
 struct RcArgs {
   const float* lw;         // FP32 log-weights, or
@@ -225,6 +227,8 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
   uint64_t* sL2 = sA + kRcChunk;                        // [kRcTpb] every 8th of them
   int32_t* sW = reinterpret_cast<int32_t*>(sL2 + kRcTpb);  // [warp][kRcItemOut] ancestors
   __shared__ uint64_t sL1[kRcChunk / 256];  // every 256th prefix sum
+  static_assert(3 * kRcJobTile * 8 <= kRcChunk * 8 + kRcTpb * 8 + kRcWarps * kRcItemOut * 4,
+                "the layout job's tile tables fit in the dynamic shared memory");
   __shared__ uint64_t wtot[kRcWarps], jtot[kRcWarps];
   __shared__ int64_t jitem[kRcWarps];
   __shared__ unsigned long long rel;
@@ -284,24 +288,23 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
   // 2. barrier: the last block scans the chunk totals, checks T, draws u, and
   // lays out the work items; the item count is the release word's payload
   const bool ok = grid_sync<true>(a.g, &a.hdr->status, G, 1, &rel, [&]() -> unsigned long long {
-    // thread tid takes chunks [c0, c1) in order
-    const int64_t per = (a.n_chunks + kRcTpb - 1) / kRcTpb;
-    const int64_t c0 = (int64_t)tid * per, c1 = c0 + per < a.n_chunks ? c0 + per : a.n_chunks;
-    // (kRcJobBlk of them loaded at once: one L2 round trip, not one each)
+    // T, the saturating sum of the chunk totals: coalesced loads, kRcJobBlk
+    // in flight per thread
     uint64_t run = 0;
-    for (int64_t b0 = c0; b0 < c1; b0 += kRcJobBlk) {
+    for (int64_t c0 = tid; c0 < a.n_chunks; c0 += (int64_t)kRcTpb * kRcJobBlk) {
       uint64_t t[kRcJobBlk];
 #pragma unroll
-      for (int r = 0; r < kRcJobBlk; ++r) t[r] = b0 + r < c1 ? __ldcg(a.ctot + b0 + r) : 0ull;
+      for (int r = 0; r < kRcJobBlk; ++r) {
+        const int64_t c = c0 + (int64_t)r * kRcTpb;
+        t[r] = c < a.n_chunks ? __ldcg(a.ctot + c) : 0ull;
+      }
 #pragma unroll
       for (int r = 0; r < kRcJobBlk; ++r) run = sat_add(run, t[r]);
     }
-    const uint64_t wi = warp_scan_u64(run, lane);
-    if (lane == 31) jtot[warp] = wi;
+    run = warp_sum_acc<false>(run);
+    if (lane == 0) jtot[warp] = run;
     __syncthreads();
-    const uint64_t jv = lane < kRcWarps ? jtot[lane] : 0ull, ji = warp_scan_u64(jv, lane);
-    const uint64_t T = __shfl_sync(0xffffffffu, ji, 31);
-    uint64_t cx = sat_add(__shfl_sync(0xffffffffu, ji - jv, warp), wi - run);
+    const uint64_t T = warp_sum_acc<false>(lane < kRcWarps ? jtot[lane] : 0ull);
     const bool valid = T > 0 && T <= (1ull << 61) && T >= (uint64_t)a.m;
     uint64_t stride = 0, u = 0;
     if (valid) {
@@ -309,65 +312,77 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
       const uint64_t w = philox_block(a.seed, 0, a.instance, a.t, kResample, 0).x;
       u = (__umul64hi(w, stride) << 32) | ((w * stride) >> 32);
     }
-    // exclusive chunk prefixes, first outputs and item costs of this thread's
-    // chunks (a chunk with outputs: its items plus kRcPrefixCost)
+    const DivInv sv = div_inv(stride);
+    // a chunk with outputs costs its items plus kRcPrefixCost
     auto cost = [](int64_t k0, int64_t k1) -> int64_t {
       return k1 > k0 ? (k1 - k0 + kRcItemOut - 1) / kRcItemOut + kRcPrefixCost : 0;
     };
-    // (a chunk's last output bound is the next chunk's first: one division
-    // per chunk).  The costs wait in shared memory (sA is unused until phase
-    // 3), or in ioff for more chunks than it holds, for the second pass.
-    int32_t* scost = reinterpret_cast<int32_t*>(sA);
-    const bool cost_smem = a.n_chunks <= 2 * kRcChunk;
-    int64_t items = 0;
-    const DivInv sv = div_inv(stride);
-    int64_t kprev = (valid && c0 < c1) ? positions_below_inv(cx, u, sv, a.m) : 0;
-    for (int64_t b0 = c0; b0 < c1; b0 += kRcJobBlk) {
-      uint64_t cs[kRcJobBlk + 1];  // the prefix at each chunk's start, then past the last
-      cs[0] = cx;
+    // Tiles of kRcJobTile chunks: the totals come into shared memory with
+    // coalesced loads; thread t takes the tile's chunks kRcJobPer t ..
+    // kRcJobPer t + kRcJobPer - 1 in order, the block scans the exclusive
+    // prefixes C, the first outputs K = positions_below(C) and the cost units
+    // (ioff); the three tables leave with coalesced stores.
+    uint64_t* jC = reinterpret_cast<uint64_t*>(rc_dyn);
+    int64_t* jK = reinterpret_cast<int64_t*>(rc_dyn + kRcJobTile * 8);
+    int64_t* jI = reinterpret_cast<int64_t*>(rc_dyn + 2 * kRcJobTile * 8);
+    uint64_t carry_c = 0;
+    int64_t carry_i = 0;
+    for (int64_t t0 = 0; t0 < a.n_chunks; t0 += kRcJobTile) {
+      const int nt = (int)(a.n_chunks - t0 < kRcJobTile ? a.n_chunks - t0 : kRcJobTile);
+      __syncthreads();  // jtot, jitem and the previous tile's tables have been read
+      for (int i = tid; i < kRcJobTile; i += kRcTpb) jC[i] = i < nt ? __ldcg(a.ctot + t0 + i) : 0ull;
+      __syncthreads();
+      uint64_t cs[kRcJobPer + 1];  // the prefix at each of this thread's chunks, then past the last
+      uint64_t own = 0;
 #pragma unroll
-      for (int r = 0; r < kRcJobBlk; ++r)
-        cs[r + 1] = sat_add(cs[r], b0 + r < c1 ? __ldcg(a.ctot + b0 + r) : 0ull);
-      int64_t kn[kRcJobBlk];  // independent divisions
+      for (int r = 0; r < kRcJobPer; ++r) own = sat_add(own, jC[tid * kRcJobPer + r]);
+      const uint64_t inc = warp_scan_u64(own, lane);
+      if (lane == 31) jtot[warp] = inc;
+      __syncthreads();
+      const uint64_t jv = lane < kRcWarps ? jtot[lane] : 0ull, ji = warp_scan_u64(jv, lane);
+      cs[0] = sat_add(carry_c, sat_add(__shfl_sync(0xffffffffu, ji - jv, warp), inc - own));
 #pragma unroll
-      for (int r = 0; r < kRcJobBlk; ++r)
-        kn[r] = (valid && b0 + r < c1) ? positions_below_inv(cs[r + 1], u, sv, a.m) : 0;
+      for (int r = 0; r < kRcJobPer; ++r) cs[r + 1] = sat_add(cs[r], jC[tid * kRcJobPer + r]);
+      int64_t k[kRcJobPer + 1];  // independent divisions
 #pragma unroll
-      for (int r = 0; r < kRcJobBlk; ++r) {
-        if (b0 + r >= c1) break;
-        const int64_t ch = b0 + r;
-        a.ctot[ch] = cs[r];
-        a.kfirst[ch] = kprev;
-        const int64_t cc = cost(kprev, kn[r]);  // < 2^31: at most m / 256 + kRcPrefixCost
-        if (cost_smem) scost[ch] = (int32_t)cc;
-        else a.ioff[ch] = cc;
-        items += cc;
-        kprev = kn[r];
-        cx = cs[r + 1];
+      for (int r = 0; r <= kRcJobPer; ++r) k[r] = valid ? positions_below_inv(cs[r], u, sv, a.m) : 0;
+      int64_t own_i = 0;
+#pragma unroll
+      for (int r = 0; r < kRcJobPer; ++r) own_i += cost(k[r], k[r + 1]);
+      int64_t ii = own_i;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, ii, o);
+        if (lane >= o) ii += y;
+      }
+      if (lane == 31) jitem[warp] = ii;
+      __syncthreads();
+      const int64_t iv = lane < kRcWarps ? jitem[lane] : 0;
+      int64_t iw = iv;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, iw, o);
+        if (lane >= o) iw += y;
+      }
+      int64_t ix = carry_i + __shfl_sync(0xffffffffu, iw - iv, warp) + (ii - own_i);
+#pragma unroll
+      for (int r = 0; r < kRcJobPer; ++r) {
+        const int e = tid * kRcJobPer + r;
+        jC[e] = cs[r];
+        jK[e] = k[r];
+        jI[e] = ix;
+        ix += cost(k[r], k[r + 1]);
+      }
+      carry_c = sat_add(carry_c, __shfl_sync(0xffffffffu, ji, 31));
+      carry_i += __shfl_sync(0xffffffffu, iw, 31);
+      __syncthreads();
+      for (int i = tid; i < nt; i += kRcTpb) {
+        a.ctot[t0 + i] = jC[i];
+        a.kfirst[t0 + i] = jK[i];
+        a.ioff[t0 + i] = jI[i];
       }
     }
-    // exclusive scan of the item counts
-    int64_t ii = items;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t y = __shfl_up_sync(0xffffffffu, ii, o);
-      if (lane >= o) ii += y;
-    }
-    if (lane == 31) jitem[warp] = ii;
-    __syncthreads();
-    int64_t iv = lane < kRcWarps ? jitem[lane] : 0, iw = iv;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int64_t y = __shfl_up_sync(0xffffffffu, iw, o);
-      if (lane >= o) iw += y;
-    }
-    int64_t ix = __shfl_sync(0xffffffffu, iw - iv, warp) + (ii - items);
-    const int64_t n_items = __shfl_sync(0xffffffffu, iw, 31);
-    for (int64_t ch = c0; ch < c1; ++ch) {  // this thread's own costs from the first pass
-      const int64_t cc = cost_smem ? (int64_t)scost[ch] : a.ioff[ch];
-      a.ioff[ch] = ix;
-      ix += cc;
-    }
+    const int64_t n_items = carry_i;
     if (tid == 0) {
       if (T == 0) record_status(&a.hdr->status, PPL_EEMPTY);
       else if (T > (1ull << 61) || T < (uint64_t)a.m) record_status(&a.hdr->status, PPL_EINVAL);
