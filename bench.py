@@ -43,7 +43,7 @@ KERNELS_PER_STEP = 3  # trace (normalisation and posterior fused), resampling, g
 # poly_trace_kernel launch on the default workload, from the full-size ncu
 # capture summarised in profiles/poly_trace_kernel_2e22x256.md; re-measure
 # whenever the kernel changes.
-TRACE_TRAFFIC_BYTES = 487424 + 541959680
+TRACE_TRAFFIC_BYTES = 3020800 + 547214080
 
 
 def parse():
