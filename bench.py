@@ -38,7 +38,7 @@ UNIT = "traces/s"
 WORKLOAD = ("linefitting likelihood weighting, 2^24 particles x 256 points, degree "
             "uniform{2..5}, coefficients N(0,10^2), sigma 0.5; + log-sum-exp/ESS + posterior "
             "reduce + systematic resampling (64-bit fixed point) + gather of 32-byte records")
-KERNELS_PER_STEP = 3  # trace (normalisation and posterior fused), resampling, gather
+KERNELS_PER_STEP = 2  # trace (normalisation and posterior fused), resampling (gather fused)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
 # poly_trace_kernel launch on the default workload, from the full-size ncu
 # capture summarised in profiles/poly_trace_kernel_2e22x256.md; re-measure
@@ -516,12 +516,10 @@ def run_ours(args):
         if ev:
             ev[1].record(stream)
             ev[2].record(stream)
-        ppl.ppl_resample_known_max(N, INFER_SEED, lw, max_lw, instance, 0, ancestors=anc, ws=ws)
+        ppl.ppl_resample_gather(N, INFER_SEED, lw, parts, max_lw_dev=max_lw, instance=instance,
+                                t=0, state_out=parts_out, ancestors=anc, ws=ws)
         if ev:
             ev[3].record(stream)
-        ppl.ppl_gather(parts, anc, state_out=parts_out)
-        if ev:
-            ev[4].record(stream)
 
     for _ in range(max(3, args.warmup)):
         step()
@@ -537,7 +535,7 @@ def run_ours(args):
     ncoef = np.arange(2, 6) + 1
     flops_per_launch = float(N_POINTS * np.sum(counts * (2 * (ncoef - 1) + 1 + 2)))
 
-    events = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     sampler = ClockSampler(gpu_index_for_smi(torch, local))
     if world > 1:
         torch.distributed.barrier()
@@ -554,7 +552,7 @@ def run_ours(args):
         torch.distributed.barrier()
     clocks = sampler.stop()
 
-    stage = np.array([[ev[i].elapsed_time(ev[i + 1]) for i in range(4)] for ev in events])
+    stage = np.array([[ev[i].elapsed_time(ev[i + 1]) for i in range(3)] for ev in events])
     step_ms = stage.sum(axis=1)
     (total_ms,) = reduce_max([float(step_ms.sum())], world, dev)
     value = weak_scaling_value(world, N, args.steps, total_ms)
@@ -572,8 +570,8 @@ def run_ours(args):
         yd.copy_(yh, non_blocking=True)
         ppl.ppl_infer_is_instance(model, xd, yd, N, INFER_SEED, instance, out=res, lw_out=lw,
                                   particles_out=parts, ws=ws)
-        ppl.ppl_resample_known_max(N, INFER_SEED, lw, max_lw, instance, 0, ancestors=anc, ws=ws)
-        ppl.ppl_gather(parts, anc, state_out=parts_out)
+        ppl.ppl_resample_gather(N, INFER_SEED, lw, parts, max_lw_dev=max_lw, instance=instance,
+                                t=0, state_out=parts_out, ancestors=anc, ws=ws)
         res_h.copy_(res, non_blocking=True)
         torch.cuda.synchronize()
     (e2e_s,) = reduce_max([time.perf_counter() - t0], world, dev)
@@ -606,7 +604,7 @@ def run_ours(args):
                      "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {max_mhz} MHz",
                      "work": "FP32 flops of the factor: L x (2 ncoef + 1) per trace"},
         "stages_ms": {"trace": trace_ms, "posterior": float(stage[:, 1].mean()),
-                      "resample": float(stage[:, 2].mean()), "gather": float(stage[:, 3].mean())},
+                      "resample_gather": float(stage[:, 2].mean())},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * N_POINTS * 4,
                 "d2h_bytes_per_step": ppl.RESULT_BYTES, "steps": n_e2e},
         "gpu_launches": KERNELS_PER_STEP * args.steps,

@@ -153,6 +153,11 @@ _SIGS = {
     "ppl_selftest_scan_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
                                                  ctypes.c_void_p, ctypes.c_size_t,
                                                  ctypes.c_void_p]),
+    "ppl_resample_gather": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                           ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
+                                           ctypes.c_uint32, ctypes.c_void_p, ctypes.c_int64,
+                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                           ctypes.c_size_t, ctypes.c_void_p]),
     "ppl_gather": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
                                   ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                   ctypes.c_void_p]),
@@ -469,6 +474,33 @@ def ppl_selftest_scan_timeout(q_fixed, max_spin, ws=None, stream=None):
 def result_max_lw(res_dev):
     """The device float64 max_lw field of a ppl_is_result buffer (no copy)."""
     return res_dev[24:32].view(torch.float64)
+
+
+def ppl_resample_gather(m, seed, lw, state_in, max_lw_dev=None, instance=0, t=0,
+                        state_out=None, ancestors=None, ws=None, stream=None):
+    """Resampling (as ppl_resample / ppl_resample_known_max) and the gather of
+    the resampled records in one call; returns (ancestors, state_out)."""
+    _dev_f32(lw, "lw")
+    if not state_in.is_contiguous():
+        raise ValueError("state_in must be contiguous")
+    n = lw.numel()
+    if state_in.shape[0] != n:
+        raise ValueError("state_in must hold one record per particle")
+    stride = state_in[0].numel() * state_in.element_size() if state_in.dim() > 1 else \
+        state_in.element_size()
+    if ws is None:
+        ws = workspace(poly_model(), max(n, m), 0, lw.device)
+    if ancestors is None:
+        ancestors = torch.empty(m, dtype=torch.int32, device=lw.device)
+    if state_out is None:
+        state_out = torch.empty((m,) + tuple(state_in.shape[1:]), dtype=state_in.dtype,
+                                device=state_in.device)
+    mx = ctypes.c_void_p(max_lw_dev.data_ptr()) if max_lw_dev is not None else None
+    st = lib().ppl_resample_gather(_ptr(lw), mx, n, int(m), ctypes.c_uint64(seed), int(instance),
+                                   int(t), _ptr(state_in), stride, _ptr(state_out),
+                                   _ptr(ancestors), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "ppl_resample_gather")
+    return ancestors, state_out
 
 
 def ppl_gather(state_in, ancestors, state_out=None, stream=None):

@@ -293,7 +293,8 @@ ppl_status ppl_logsumexp(const float* lw, int64_t n, double* out_dev, void* ws, 
 static ppl_status resample_impl(const float* lw, const uint64_t* q_fixed, const double* known_max,
                                 int64_t n, int64_t m, uint64_t seed, uint32_t instance,
                                 uint32_t t, int32_t* ancestors, void* ws, size_t ws_bytes,
-                                ppl_stream stream) {
+                                ppl_stream stream, const void* rec_in = nullptr,
+                                int64_t rec_bytes = 0, void* rec_out = nullptr) {
   if ((lw == nullptr) == (q_fixed == nullptr)) return PPL_EINVAL;
   if (!ancestors || n < 1 || n > kMaxParticles || m < 1 || m > kMaxParticles) return PPL_EINVAL;
   Ws w;
@@ -307,8 +308,26 @@ static ppl_status resample_impl(const float* lw, const uint64_t* q_fixed, const 
   // tables (a few bytes per 4096 particles)
   PPL_TRY(cuda_status(launch_resample_coop(lw, q_fixed, known_max, n, m, seed, instance, t,
                                            w.hdr(), w.tiles(), reinterpret_cast<char*>(w.prefix()),
-                                           w.l.bounds - w.l.prefix, ancestors, nullptr, s)));
+                                           w.l.bounds - w.l.prefix, ancestors, nullptr, s, rec_in,
+                                           rec_bytes, rec_out)));
   return PPL_OK;
+}
+
+ppl_status ppl_resample_gather(const float* lw, const double* max_lw_dev, int64_t n, int64_t m,
+                               uint64_t seed, uint32_t instance, uint32_t t, const void* state_in,
+                               int64_t stride_bytes, void* state_out, int32_t* ancestors,
+                               void* ws, size_t ws_bytes, ppl_stream stream) {
+  if (!lw || !state_in || !state_out || stride_bytes <= 0) return PPL_EINVAL;
+  const bool fused = stride_bytes % 16 == 0 && stride_bytes <= 1024 &&
+                     ((reinterpret_cast<uintptr_t>(state_in) |
+                       reinterpret_cast<uintptr_t>(state_out)) & 15) == 0;
+  if (fused)
+    return resample_impl(lw, nullptr, max_lw_dev, n, m, seed, instance, t, ancestors, ws,
+                         ws_bytes, stream, state_in, stride_bytes, state_out);
+  PPL_TRY(resample_impl(lw, nullptr, max_lw_dev, n, m, seed, instance, t, ancestors, ws, ws_bytes,
+                        stream));
+  return cuda_status(launch_gather(state_in, n, stride_bytes, ancestors, m, state_out, nullptr,
+                                   (cudaStream_t)stream));
 }
 
 ppl_status ppl_resample(const float* lw, const uint64_t* q_fixed, int64_t n, int64_t m,

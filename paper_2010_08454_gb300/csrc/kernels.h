@@ -83,16 +83,20 @@ cudaError_t launch_smc_propagate(const LgssmParams& p, float y_t, int32_t t, uin
                                  int32_t* resampled, double* logz_est, WsHeader* hdr,
                                  void* parts, cudaStream_t s);
 size_t smc_run_workspace(int64_t N, int64_t T);
-// Systematic resampling in one cooperative kernel (ancestors only).
-// `barrier` holds the grid barrier's words (resample_coop_barrier_bytes(),
-// 128-byte aligned, zeroed by the caller before the launch); `scratch` the
-// per-chunk tables (resample_coop_scratch(n) bytes, 16-byte aligned).
+// Systematic resampling in one cooperative kernel: the ancestors, and with
+// rec_in the gathered records too (rec_out[k] = rec_in[anc[k]], rec_bytes a
+// multiple of 16 up to 1024, both pointers 16-byte aligned).  `barrier` holds
+// the grid barrier's words (resample_coop_barrier_bytes(), 128-byte aligned,
+// zeroed by the caller before the launch); `scratch` the per-chunk tables
+// (resample_coop_scratch(n) bytes, 16-byte aligned).
 size_t resample_coop_scratch(int64_t n);
 size_t resample_coop_barrier_bytes();
 cudaError_t launch_resample_coop(const float* lw, const uint64_t* q_fixed, const double* known_max,
                                  int64_t n, int64_t m, uint64_t seed, uint32_t instance, uint32_t t,
                                  WsHeader* hdr, void* barrier, char* scratch, size_t scratch_bytes,
-                                 int32_t* anc, const int32_t* gate, cudaStream_t s);
+                                 int32_t* anc, const int32_t* gate, cudaStream_t s,
+                                 const void* rec_in = nullptr, int64_t rec_bytes = 0,
+                                 void* rec_out = nullptr);
 cudaError_t launch_smc_persistent(const LgssmParams& p, const float* y, int32_t T, uint64_t seed,
                                   int64_t N, float* x_out, float* lw_out, double* logz,
                                   int32_t* resampled, double* ess, char* ws, size_t ws_bytes,

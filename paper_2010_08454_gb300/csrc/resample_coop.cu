@@ -63,7 +63,32 @@ struct RcArgs {
   uint64_t* ctot;   // [n_chunks] chunk totals, then their exclusive prefix
   int64_t* kfirst;  // [n_chunks + 1] first output of each chunk (K_c), K_last = m
   int64_t* ioff;    // [n_chunks + 1] first work item of each chunk
+  // fused gather (rec_words > 0): rec_out[k] = rec_in[a_k], records of
+  // rec_words 16-byte words, rec_in holding the n particles' records
+  const uint4* rec_in;
+  uint4* rec_out;
+  int32_t rec_words;
 };
+
+// The records of outputs k0 .. k0 + nB - 1 of an item, by one warp: output j
+// copies the record of ancestor anc_of(j); consecutive lanes take consecutive
+// 16-byte words, so both the loads (ancestors are non-decreasing) and the
+// stores are coalesced.
+template <class AncOf>
+__device__ __forceinline__ void gather_item(const RcArgs& a, int64_t k0, int nB, AncOf anc_of,
+                                            int lane) {
+  const int W = a.rec_words;
+  const int total = nB * W;
+  uint4* out = a.rec_out + k0 * W;
+  if (W == 2) {
+    for (int e = lane; e < total; e += 32) out[e] = a.rec_in[(int64_t)anc_of(e >> 1) * 2 + (e & 1)];
+  } else {
+    for (int e = lane; e < total; e += 32) {
+      const int j = e / W;
+      out[e] = a.rec_in[(int64_t)anc_of(j) * W + (e - j * W)];
+    }
+  }
+}
 
 // The weights of one thread's kRcItems particles from `base`: FP32
 // log-weights (raw, -inf past n) or given fixed-point words (0 past n).
@@ -457,6 +482,7 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
         if (posl < sA[ia]) {  // one ancestor for the whole item (degenerate weights)
           const int32_t an = (int32_t)(cb + ia);
           for (int jj = lane; jj < nB; jj += 32) a.anc[k0 + jj] = an;
+          if (a.rec_words > 0) gather_item(a, k0, nB, [an](int) { return an; }, lane);
           continue;
         }
         const int ib = min(chunk_first_above(sA, sL2, sL1, posl, lane) + 1, nC);
@@ -485,6 +511,7 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
         }
         __syncwarp();
         for (int jj = lane; jj < nB; jj += 32) a.anc[k0 + jj] = sWw[jj];
+        if (a.rec_words > 0) gather_item(a, k0, nB, [sWw](int j) { return sWw[j]; }, lane);
         __syncwarp();  // sWw is rewritten by the warp's next item
       }
     }
@@ -503,7 +530,8 @@ size_t resample_coop_barrier_bytes() { return sizeof(GridCtl); }
 cudaError_t launch_resample_coop(const float* lw, const uint64_t* q_fixed, const double* known_max,
                                  int64_t n, int64_t m, uint64_t seed, uint32_t instance, uint32_t t,
                                  WsHeader* hdr, void* barrier, char* scratch, size_t scratch_bytes,
-                                 int32_t* anc, const int32_t* gate, cudaStream_t s) {
+                                 int32_t* anc, const int32_t* gate, cudaStream_t s,
+                                 const void* rec_in, int64_t rec_bytes, void* rec_out) {
   if (scratch_bytes < resample_coop_scratch(n) || (reinterpret_cast<uintptr_t>(scratch) & 15) ||
       (reinterpret_cast<uintptr_t>(barrier) & 127))
     return cudaErrorInvalidValue;
@@ -520,6 +548,15 @@ cudaError_t launch_resample_coop(const float* lw, const uint64_t* q_fixed, const
   a.anc = anc;
   a.gate = gate;
   a.n_chunks = (n + kRcChunk - 1) / kRcChunk;
+  a.rec_in = reinterpret_cast<const uint4*>(rec_in);
+  a.rec_out = reinterpret_cast<uint4*>(rec_out);
+  a.rec_words = 0;
+  if (rec_in) {
+    if (!rec_out || rec_bytes <= 0 || rec_bytes % 16 || rec_bytes / 16 > 64 ||
+        ((reinterpret_cast<uintptr_t>(rec_in) | reinterpret_cast<uintptr_t>(rec_out)) & 15))
+      return cudaErrorInvalidValue;
+    a.rec_words = (int32_t)(rec_bytes / 16);
+  }
   size_t off = 0;
   auto take = [&](size_t bytes) {
     char* q = scratch + off;

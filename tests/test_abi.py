@@ -93,4 +93,9 @@ def test_host_side_argument_checks(ppl):
     assert lib.ppl_smc_step(ctypes.byref(lg), 0.0, 0, 0, args[0], args[1], 10, args[2], args[3],
                             args[4], ctypes.c_void_p(256), 1 << 30, None) == ppl.PPL_EINVAL
     assert lib.ppl_gather(None, 10, 4, None, 10, None, None) == ppl.PPL_EINVAL
+    # resample + gather: lw, both record buffers and a positive stride required
+    v = ctypes.c_void_p(256)
+    for lw_, si, so, st in [(None, v, v, 32), (v, None, v, 32), (v, v, None, 32), (v, v, v, 0)]:
+        assert lib.ppl_resample_gather(lw_, None, 10, 10, 0, 0, 0, si, st, so, v, v, 1 << 30,
+                                       None) == ppl.PPL_EINVAL
     assert lib.ppl_rng_words(0, 0, 0, 1, 10, 2, ctypes.c_void_p(8), None) == ppl.PPL_EINVAL

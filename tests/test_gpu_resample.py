@@ -96,6 +96,28 @@ def test_device_errors_are_reported(ppl):
     torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("kind", ["normal", "onehot", "sparse"])
+@pytest.mark.parametrize("N,M", [(1, 1), (4099, 4099), (100003, 100780), (262147, 70001)])
+@pytest.mark.parametrize("rec", ["f32x8", "f32x12", "i16x8", "f32x3"])
+def test_resample_gather_bit_exact(ppl, orc, kind, N, M, rec):
+    # 32-, 48- and 16-byte records take the fused path, 12-byte ones the
+    # separate gather; ancestors and records against the oracle, bit for bit
+    import torch
+    rng = np.random.default_rng(N + M)
+    cols, dtype = {"f32x8": (8, np.float32), "f32x12": (12, np.float32),
+                   "i16x8": (8, np.int16), "f32x3": (3, np.float32)}[rec]
+    state = rng.integers(-30000, 30000, (N, cols)).astype(dtype)
+    lw = synth.log_weights(N, 7 + N, kind)
+    st, anc_ref = orc.resample_from_lw(lw, M, 13, 1, 3)
+    assert st == 0
+    for known in (False, True):
+        mx = torch.tensor([float(lw.max())], dtype=torch.float64, device="cuda") if known else None
+        anc, out = ppl.ppl_resample_gather(M, 13, _t(lw), _t(state), max_lw_dev=mx, instance=1,
+                                           t=3)
+        assert np.array_equal(anc.cpu().numpy(), anc_ref)
+        assert np.array_equal(out.cpu().numpy(), orc.gather(state, anc_ref))
+
+
 def test_known_max_below_a_log_weight_is_reported(ppl):
     import torch
     lw = synth.log_weights(10000, 5, "normal")
