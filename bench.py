@@ -44,6 +44,9 @@ KERNELS_PER_STEP = 2  # trace (normalisation and posterior fused), resampling (g
 # capture summarised in profiles/poly_trace_kernel_2e22x256.md; re-measure
 # whenever the kernel changes.
 TRACE_TRAFFIC_BYTES = 3020800 + 547214080
+# The same for the resampling kernel with the gather fused (profiles/
+# resample_coop_kernel_2e22.md); None until measured on the current kernel.
+RG_TRAFFIC_BYTES = None
 
 
 def parse():
@@ -58,7 +61,8 @@ def parse():
                     help="skip the state-space, batched and learned-proposal workloads")
     ap.add_argument("--particles", type=int, default=N_PARTICLES,
                     help="particles per step (smaller cases for profiling only)")
-    ap.add_argument("--config", choices=["smc", "batched", "learned", "suffstat", "small"],
+    ap.add_argument("--config", choices=["smc", "batched", "learned", "suffstat", "small",
+                                         "normalise"],
                     help="run only this secondary workload and print its line (profiling)")
     return ap.parse_args()
 
@@ -300,6 +304,34 @@ def bench_suffstat(torch, ppl, reps=10):
             "unit": "traces/s", "ms_per_launch": times["suffstat"],
             "direct_ms_per_launch": times["direct"], "log_z": summary["log_z"],
             "gpu_launches_per_call": 2}
+
+
+def bench_normalise(torch, ppl, reps=20):
+    """The normalisation pass on its own (ppl_logsumexp: max, log-sum-exp, ESS
+    and argmax of 2^24 FP32 log-weights, one read of lw), against the measured
+    HBM bandwidth; L2 flushed before every timed call."""
+    import numpy as np
+
+    import synth
+    N = N_PARTICLES
+    lw = torch.from_numpy(synth.log_weights(N, 12, "normal", scale=20.0)).cuda()
+    ws = ppl.workspace(ppl.poly_model(), N, 0)
+    out = torch.empty(4, dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        ppl.ppl_logsumexp(lw, out=out, ws=ws)
+    t = []
+    for _ in range(reps):
+        flush.fill_(1)
+        t.append(_event_ms(torch, lambda: ppl.ppl_logsumexp(lw, out=out, ws=ws), 1))
+    ms = float(np.median(t))
+    gbs = N * 4 / (ms / 1e3) / 1e9
+    peak = (load_peaks() or {}).get("hbm_gbs")
+    return {"workload": "log-sum-exp, ESS, max and argmax of 2^24 FP32 log-weights "
+                        "(one pass; the headline step fuses it into the trace kernel)",
+            "metric": "GB/s of log-weights read", "value": gbs, "unit": "GB/s",
+            "ms_per_call": ms, "hbm_peak_gbs": peak, "frac": gbs / peak if peak else None,
+            "gpu_launches_per_call": 1}
 
 
 def bench_small_models(torch, ppl, reps=10):
@@ -582,6 +614,12 @@ def run_ours(args):
     if rank != 0:
         return 0
 
+    # the fused resampling + gather stage against HBM: algorithmic bytes = lw
+    # read, ancestors and records written, each distinct ancestor's record read
+    rec_bytes = parts[0].numel() * parts.element_size()
+    distinct = int(torch.unique(anc).numel())
+    rg_bytes = N * (4 + 4 + rec_bytes) + distinct * rec_bytes
+    rg_ms = float(stage[:, 2].mean())
     peaks = load_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     max_mhz = (peaks or {}).get("sm_max_mhz", 2070.0)
@@ -604,7 +642,18 @@ def run_ours(args):
                      "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {max_mhz} MHz",
                      "work": "FP32 flops of the factor: L x (2 ncoef + 1) per trace"},
         "stages_ms": {"trace": trace_ms, "posterior": float(stage[:, 1].mean()),
-                      "resample_gather": float(stage[:, 2].mean())},
+                      "resample_gather": rg_ms},
+        "roofline_resample_gather": {
+            "kernel": "resample_coop_kernel (gather fused)", "bound": "hbm",
+            "achieved": rg_bytes / (rg_ms / 1e3) / 1e9,
+            "peak": (peaks or {}).get("hbm_gbs", 6800.0), "unit": "GB/s",
+            "frac": rg_bytes / (rg_ms / 1e3) / 1e9 / (peaks or {}).get("hbm_gbs", 6800.0),
+            "peak_source": "measured copy bandwidth" if peaks else "fallback",
+            "bytes_per_step": rg_bytes, "distinct_ancestors": distinct,
+            "traffic": RG_TRAFFIC_BYTES if N == N_PARTICLES else None,
+            "traffic_unit": "bytes per launch",
+            "work": "lw 4 B in, ancestor 4 B and record out per particle; each distinct "
+                    "ancestor's record in"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 2 * N_POINTS * 4,
                 "d2h_bytes_per_step": ppl.RESULT_BYTES, "steps": n_e2e},
         "gpu_launches": KERNELS_PER_STEP * args.steps,
@@ -616,6 +665,7 @@ def run_ours(args):
         out["configs"] = {"smc_lgssm_T200_2e20": bench_smc(torch, ppl),
                           "suffstat_linefitting_2e24x256": bench_suffstat(torch, ppl),
                           "small_models_2e24": bench_small_models(torch, ppl),
+                          "normalise_2e24": bench_normalise(torch, ppl),
                           "batched_4096": bench_batched(torch, ppl),
                           "learned_proposal_1024x2e20": bench_learned(torch, ppl)}
     if not args.no_cpu_baseline:
@@ -631,7 +681,8 @@ def run_config(args):
     torch.cuda.set_device(0)
     ppl.lib()
     fn = {"smc": bench_smc, "batched": bench_batched, "learned": bench_learned,
-          "suffstat": bench_suffstat, "small": bench_small_models}[args.config]
+          "suffstat": bench_suffstat, "small": bench_small_models,
+          "normalise": bench_normalise}[args.config]
     print(json.dumps({"config": args.config, "result": fn(torch, ppl)}), flush=True)
     return 0
 

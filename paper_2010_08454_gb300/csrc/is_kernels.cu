@@ -121,13 +121,73 @@ __global__ void __launch_bounds__(kTpb, 4) poly_trace_kernel(
 // ---------------------------------------------------------------------------
 // Statistics pass over an existing set of log-weights (lw NULL = all 0).
 // ---------------------------------------------------------------------------
+constexpr int kStatVec = 4;  // float4 loads per thread per round: 16 log-weights in flight
+
+// A thread's batch of log-weights (lowest index first) folded into its running
+// statistics: the batch maximum (lowest index on ties) rescales the sums once,
+// then every finite weight adds exp(lw - m) and its square; NaNs only raise the
+// flag.  Indices increase from batch to batch, so ties keep the earlier index.
+template <int B>
+__device__ __forceinline__ void add_batch(StatAcc& acc, const float (&v)[B], int64_t i0,
+                                          int64_t step) {
+  float mb = -INFINITY;
+  int64_t ib = 0x7fffffff;
+#pragma unroll
+  for (int j = 0; j < B; ++j) {
+    acc.nan |= v[j] != v[j];
+    if (v[j] > mb) {
+      mb = v[j];
+      ib = i0 + (j / 4) * step + (j % 4);
+    }
+  }
+  if (mb > acc.m) {
+    const float e = (acc.m == -INFINITY) ? 0.0f : expf(acc.m - mb);
+    acc.s *= e;
+    acc.s2 *= e * e;
+    acc.m = mb;
+    acc.arg = (int)ib;
+  }
+  if (acc.m > -INFINITY) {
+#pragma unroll
+    for (int j = 0; j < B; ++j) {
+      if (v[j] > -INFINITY) {  // NaN and -inf add nothing
+        const float e = expf(v[j] - acc.m);
+        acc.s += e;
+        acc.s2 = fmaf(e, e, acc.s2);
+      }
+    }
+  }
+}
+
 __global__ void __launch_bounds__(kTpb) stats_kernel(const float* __restrict__ lw, int64_t N,
                                                      WsHeader* hdr, StatPartial* parts,
                                                      double* lse_out) {
   StatAcc acc;
   acc.init();
   const int64_t stride = (int64_t)gridDim.x * kTpb;
-  for (int64_t i = (int64_t)blockIdx.x * kTpb + threadIdx.x; i < N; i += stride)
+  int64_t done = 0;  // the prefix handled by the vector loop
+  if (lw && (reinterpret_cast<uintptr_t>(lw) & 15) == 0) {
+    // coalesced 16-byte loads, kStatVec of them in flight per thread; thread t
+    // of the grid takes vectors t, t + stride, ..., kStatVec per round
+    const float4* v4 = reinterpret_cast<const float4*>(lw);
+    const int64_t n4 = N / 4;
+    const int64_t round = stride * kStatVec;
+    const int64_t full = n4 / round * round;  // vectors in whole rounds
+    for (int64_t q = (int64_t)blockIdx.x * kTpb + threadIdx.x; q < full; q += round) {
+      float v[4 * kStatVec];
+#pragma unroll
+      for (int r = 0; r < kStatVec; ++r) {
+        const float4 x = __ldcs(v4 + q + r * stride);
+        v[4 * r] = x.x;
+        v[4 * r + 1] = x.y;
+        v[4 * r + 2] = x.z;
+        v[4 * r + 3] = x.w;
+      }
+      add_batch<4 * kStatVec>(acc, v, 4 * q, 4 * stride);
+    }
+    done = 4 * full;
+  }
+  for (int64_t i = done + (int64_t)blockIdx.x * kTpb + threadIdx.x; i < N; i += stride)
     acc.add(lw ? lw[i] : 0.0f, (int)i, -1);
   StatAcc r = block_reduce_stat(acc);
   if (threadIdx.x == 0) to_partial(r, parts + blockIdx.x);
