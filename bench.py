@@ -45,8 +45,8 @@ KERNELS_PER_STEP = 2  # trace (normalisation and posterior fused), resampling (g
 # whenever the kernel changes.
 TRACE_TRAFFIC_BYTES = 3020800 + 547214080
 # The same for the resampling kernel with the gather fused (profiles/
-# resample_coop_kernel_2e22.md); None until measured on the current kernel.
-RG_TRAFFIC_BYTES = None
+# resample_coop_kernel_2e22.md); re-measure whenever the kernel changes.
+RG_TRAFFIC_BYTES = 67785472 + 542437120
 
 
 def parse():
