@@ -43,7 +43,7 @@ KERNELS_PER_STEP = 2  # trace (normalisation and posterior fused), resampling (g
 # poly_trace_kernel launch on the default workload, from the full-size ncu
 # capture summarised in profiles/poly_trace_kernel_2e22x256.md; re-measure
 # whenever the kernel changes.
-TRACE_TRAFFIC_BYTES = 3020800 + 547214080
+TRACE_TRAFFIC_BYTES = 3329792 + 547968512
 # The same for the resampling kernel with the gather fused (profiles/
 # resample_coop_kernel_2e22.md); re-measure whenever the kernel changes.
 RG_TRAFFIC_BYTES = 67785472 + 542437120

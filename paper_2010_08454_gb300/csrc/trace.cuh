@@ -107,6 +107,16 @@ __device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsig
   return d;
 }
 
+// One 32-byte record in a single 256-bit store (sm_100 and later; p 32-byte
+// aligned): a warp's 32 consecutive records are then 32 whole sectors per
+// instruction instead of two half-filled ones each.
+__device__ __forceinline__ void st_global_v8(void* p, float a, float b, float c, float d, float e,
+                                             float f, float g, float h) {
+  asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(p), "f"(a),
+               "f"(b), "f"(c), "f"(d), "f"(e), "f"(f), "f"(g), "f"(h)
+               : "memory");
+}
+
 // ss += sum over the staged points of (y - f(x))^2, f by Horner's rule over NC
 // coefficients, for PPT traces at once (in pairs when PPT is even: the
 // results are those of the scalar chain, bit for bit).  Inner sums of 16
@@ -334,6 +344,105 @@ struct PriorDraw {
   }
 };
 
+// A warp's candidates for its per-degree partials (phase C of trace_group).
+template <int PPT>
+struct Cands {
+  float lw[PPT];
+  int deg[PPT];
+  int slot[PPT];
+  unsigned cmask[PPT];
+};
+
+// More than kSerialMerges candidates folded into the warp's per-degree
+// partials by warp reductions, one degree at a time.
+template <int PPT>
+__device__ __forceinline__ void merge_full(TraceSmem<PPT>* ts, const Cands<PPT> cd, int warp,
+                                        int lane) {
+  // the degrees that have candidates in this warp
+  unsigned dmask = 0;
+#pragma unroll
+  for (int j = 0; j < PPT; ++j)
+    if ((cd.cmask[j] >> lane) & 1u) dmask |= 1u << cd.deg[j];
+  dmask = __reduce_or_sync(0xffffffffu, dmask);
+  for (int dd = 0; dd < kMaxDegrees; ++dd) {
+    if (!((dmask >> dd) & 1u)) continue;
+    float m = -INFINITY;
+    int a = 0x7fffffff, as = -1;
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      const bool cj = (cd.cmask[j] >> lane) & 1u;
+      if (cj && cd.deg[j] == dd) {
+        const int ij = ts->idx[cd.slot[j]];
+        if (cd.lw[j] > m || (cd.lw[j] == m && ij < a)) {
+          m = cd.lw[j];
+          a = ij;
+          as = cd.slot[j];
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float om = __shfl_xor_sync(0xffffffffu, m, o);
+      const int oa = __shfl_xor_sync(0xffffffffu, a, o);
+      const int os = __shfl_xor_sync(0xffffffffu, as, o);
+      if (om > m || (om == m && oa < a)) {
+        m = om;
+        a = oa;
+        as = os;
+      }
+    }
+    if (!(m > -INFINITY)) continue;  // no finite candidate of this degree
+    float ref[kMaxCoef];
+#pragma unroll
+    for (int k = 0; k < kMaxCoef; ++k) ref[k] = ts->c[as * kCStride + k];
+    float S = 0.0f, S2 = 0.0f, A[kMaxCoef], B[kMaxCoef];
+#pragma unroll
+    for (int k = 0; k < kMaxCoef; ++k) {
+      A[k] = 0.0f;
+      B[k] = 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+      const bool cj = (cd.cmask[j] >> lane) & 1u;
+      if (!cj || cd.deg[j] != dd) continue;
+      const float w = (cd.lw[j] > -INFINITY) ? expf(cd.lw[j] - m) : 0.0f;
+      S += w;
+      S2 = fmaf(w, w, S2);
+#pragma unroll
+      for (int k = 0; k < kMaxCoef; ++k) {
+        const float dc = ts->c[cd.slot[j] * kCStride + k] - ref[k];
+        const float t = w * dc;
+        A[k] += t;
+        B[k] = fmaf(t, dc, B[k]);
+      }
+    }
+    S = warp_sum(S);
+    S2 = warp_sum(S2);
+#pragma unroll
+    for (int k = 0; k < kMaxCoef; ++k) {
+      A[k] = warp_sum(A[k]);
+      B[k] = warp_sum(B[k]);
+    }
+    if (lane == 0) {
+      DegPartial r;
+      deg_empty(r);
+      r.m = m;
+      r.arg = a;
+      r.S = S;
+      r.S2 = S2;
+      if (S > 0.0f) {
+#pragma unroll
+        for (int k = 0; k < kMaxCoef; ++k) {
+          const float sh = A[k] / S;
+          r.mean[k] = ref[k] + sh;
+          r.M2[k] = fmaxf(B[k] - sh * A[k], 0.0f);
+        }
+      }
+      deg_merge(ts->wrun[warp * kMaxDegrees + dd], r);
+    }
+  }
+}
+
 // Runs traces [base, base + kTpb * PPT) of an instance with N traces and merges
 // them into the warps' running per-degree partials (ts.wrun).  Data: L points at xs, ys; when
 // `resident` the caller has staged all of them in sdata, otherwise they
@@ -348,6 +457,7 @@ __device__ __forceinline__ void trace_group(const Draw& draw, const PolyParams& 
                                             TraceSmem<PPT>& ts, const SuffStat* suff = nullptr) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned lt = (1u << lane) - 1u;
+  const bool rec_v8 = (reinterpret_cast<uintptr_t>(rec_out) & 31) == 0;
   // A. draw, write the records, rank every trace within its degree
   float c[PPT][kMaxCoef], corr[PPT];
   int d[PPT], rank[PPT];
@@ -357,9 +467,14 @@ __device__ __forceinline__ void trace_group(const Draw& draw, const PolyParams& 
     const int n = draw((uint32_t)(i < N ? i : 0), c[q], corr[q]);
     d[q] = (i < N) ? n - p.min_deg : -1;
     if (i < N && rec_out) {
-      float4* dst = reinterpret_cast<float4*>(rec_out + i);
-      dst[0] = make_float4(c[q][0], c[q][1], c[q][2], c[q][3]);
-      dst[1] = make_float4(c[q][4], c[q][5], __int_as_float(n), __uint_as_float((uint32_t)i));
+      if (rec_v8) {
+        st_global_v8(rec_out + i, c[q][0], c[q][1], c[q][2], c[q][3], c[q][4], c[q][5],
+                     __int_as_float(n), __uint_as_float((uint32_t)i));
+      } else {
+        float4* dst = reinterpret_cast<float4*>(rec_out + i);
+        dst[0] = make_float4(c[q][0], c[q][1], c[q][2], c[q][3]);
+        dst[1] = make_float4(c[q][4], c[q][5], __int_as_float(n), __uint_as_float((uint32_t)i));
+      }
     }
 #pragma unroll
     for (int k = 0; k < kMaxDegrees; ++k) {
@@ -518,89 +633,15 @@ __device__ __forceinline__ void trace_group(const Draw& draw, const PolyParams& 
       }
     }
   } else if (ncand > kSerialMerges) {
-    // the degrees that have candidates in this warp
-    unsigned dmask = 0;
+    Cands<PPT> cd;
 #pragma unroll
-    for (int j = 0; j < PPT; ++j)
-      if ((cmask[j] >> lane) & 1u) dmask |= 1u << deg[j];
-    dmask = __reduce_or_sync(0xffffffffu, dmask);
-    for (int dd = 0; dd < kMaxDegrees; ++dd) {
-      if (!((dmask >> dd) & 1u)) continue;
-      float m = -INFINITY;
-      int a = 0x7fffffff, as = -1;
-#pragma unroll
-      for (int j = 0; j < PPT; ++j) {
-        const bool cj = (cmask[j] >> lane) & 1u;
-        if (cj && deg[j] == dd) {
-          const int ij = ts.idx[slot[j]];
-          if (lw[j] > m || (lw[j] == m && ij < a)) {
-            m = lw[j];
-            a = ij;
-            as = slot[j];
-          }
-        }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float om = __shfl_xor_sync(0xffffffffu, m, o);
-        const int oa = __shfl_xor_sync(0xffffffffu, a, o);
-        const int os = __shfl_xor_sync(0xffffffffu, as, o);
-        if (om > m || (om == m && oa < a)) {
-          m = om;
-          a = oa;
-          as = os;
-        }
-      }
-      if (!(m > -INFINITY)) continue;  // no finite candidate of this degree
-      float ref[kMaxCoef];
-#pragma unroll
-      for (int k = 0; k < kMaxCoef; ++k) ref[k] = ts.c[as * kCStride + k];
-      float S = 0.0f, S2 = 0.0f, A[kMaxCoef], B[kMaxCoef];
-#pragma unroll
-      for (int k = 0; k < kMaxCoef; ++k) {
-        A[k] = 0.0f;
-        B[k] = 0.0f;
-      }
-#pragma unroll
-      for (int j = 0; j < PPT; ++j) {
-        const bool cj = (cmask[j] >> lane) & 1u;
-        if (!cj || deg[j] != dd) continue;
-        const float w = (lw[j] > -INFINITY) ? expf(lw[j] - m) : 0.0f;
-        S += w;
-        S2 = fmaf(w, w, S2);
-#pragma unroll
-        for (int k = 0; k < kMaxCoef; ++k) {
-          const float dc = ts.c[slot[j] * kCStride + k] - ref[k];
-          const float t = w * dc;
-          A[k] += t;
-          B[k] = fmaf(t, dc, B[k]);
-        }
-      }
-      S = warp_sum(S);
-      S2 = warp_sum(S2);
-#pragma unroll
-      for (int k = 0; k < kMaxCoef; ++k) {
-        A[k] = warp_sum(A[k]);
-        B[k] = warp_sum(B[k]);
-      }
-      if (lane == 0) {
-        DegPartial r;
-        deg_empty(r);
-        r.m = m;
-        r.arg = a;
-        r.S = S;
-        r.S2 = S2;
-        if (S > 0.0f) {
-#pragma unroll
-          for (int k = 0; k < kMaxCoef; ++k) {
-            const float sh = A[k] / S;
-            r.mean[k] = ref[k] + sh;
-            r.M2[k] = fmaxf(B[k] - sh * A[k], 0.0f);
-          }
-        }
-        deg_merge(ts.wrun[warp * kMaxDegrees + dd], r);
-      }
+    for (int j = 0; j < PPT; ++j) {
+      cd.lw[j] = lw[j];
+      cd.deg[j] = deg[j];
+      cd.slot[j] = slot[j];
+      cd.cmask[j] = cmask[j];
     }
+    merge_full<PPT>(&ts, cd, warp, lane);
   }
   nan = __any_sync(0xffffffffu, nan);
   if (lane == 0 && nan) ts.nan = 1;
