@@ -64,7 +64,7 @@ static BatchLayout batch_layout(int64_t n_items, int32_t n_inst) {
 constexpr int kBatchChunk = 4096;  // data points staged in shared memory at a time
 
 template <int PPT, bool LEARNED>
-__global__ void __launch_bounds__(kTpb, PPT >= 8 ? 2 : 3) batched_kernel(
+__global__ void __launch_bounds__(kTpb, PPT >= 8 ? 2 : (LEARNED ? 3 : 4)) batched_kernel(
     PolyParams p, const float* __restrict__ xs, const float* __restrict__ ys,
     const int64_t* __restrict__ data_off, const int64_t* __restrict__ part_off,
     const BatchItem* __restrict__ items, int64_t n_items, const int32_t* __restrict__ first,
