@@ -78,6 +78,26 @@ def test_logsumexp(ppl, orc, N):
     assert out[2] == ref["max_lw"] and int(out[3]) == ref["argmax"]
 
 
+@pytest.mark.parametrize("N", [16, 100003, 1 << 20])
+def test_logsumexp_ties_and_misaligned_input(ppl, orc, N):
+    # the maximum at several indices: the lowest wins, in the vector path and in
+    # the scalar path a misaligned view takes (offset by one float)
+    lw = synth.log_weights(N + 1, 9, "normal", scale=3.0)
+    peak = float(lw.max()) + 1.0
+    for j in (N // 3, N // 2, N - 1):
+        lw[j + 1] = peak
+    dev = _t(lw)
+    for t, view in ((dev[1:], lw[1:]), (dev[:N], lw[:N])):  # 4 bytes off 16-byte alignment, aligned
+        out = ppl.ppl_logsumexp(t).cpu().numpy()
+        ref = orc.lse_ess(view.astype(np.float64))
+        assert out[0] == pytest.approx(ref["lse"], abs=1e-5)
+        assert out[1] == pytest.approx(ref["ess"], rel=1e-5)
+        assert out[2] == ref["max_lw"] and int(out[3]) == ref["argmax"]
+    const = _t(np.zeros(N, dtype=np.float32))
+    out = ppl.ppl_logsumexp(const).cpu().numpy()
+    assert int(out[3]) == 0 and out[1] == pytest.approx(N, rel=1e-6)
+
+
 def test_device_errors_are_reported(ppl):
     import torch
     lw = np.zeros(5000, dtype=np.float32)
