@@ -265,7 +265,9 @@ def bench_smc(torch, ppl, reps=5):
             "log_z": logz, "kalman_log_z": kal, "abs_err_vs_kalman": abs(logz - kal),
             "gpu_launches_per_filter": 1,
             "stepwise_graph": {"ms_per_filter": ms_steps, "log_z": logz_steps,
-                               "gpu_launches_per_filter": 5 * T,
+                               # per step: propagate, resampling with the
+                               # state gather fused, commit
+                               "gpu_launches_per_filter": 3 * T,
                                "same_particles": bool(torch.equal(out["x"], x))}}
 
 

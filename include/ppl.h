@@ -265,10 +265,10 @@ ppl_status ppl_resample_known_max(const float* lw, const double* max_lw_dev, int
  * ppl_resample_known_max written to ancestors [dev, int32, m], and
  * state_out[k] = state_in[ancestors[k]] for k < m, records of stride_bytes
  * bytes [dev]; state_in holds the n particles' records.  Records whose size
- * is a multiple of 16 bytes (up to 1024) with 16-byte aligned buffers are
+ * is a multiple of 4 bytes (up to 1024) with 4-byte aligned buffers are
  * copied by the resampling kernel's own work items as their ancestors are
- * found; other records go through ppl_gather after it.  Errors as
- * ppl_resample and ppl_gather. */
+ * found (in 16-byte words when size and buffers allow); other records go
+ * through ppl_gather after it.  Errors as ppl_resample and ppl_gather. */
 ppl_status ppl_resample_gather(const float* lw, const double* max_lw_dev, int64_t n, int64_t m,
                                uint64_t seed, uint32_t instance, uint32_t t, const void* state_in,
                                int64_t stride_bytes, void* state_out, int32_t* ancestors,

@@ -318,9 +318,9 @@ ppl_status ppl_resample_gather(const float* lw, const double* max_lw_dev, int64_
                                int64_t stride_bytes, void* state_out, int32_t* ancestors,
                                void* ws, size_t ws_bytes, ppl_stream stream) {
   if (!lw || !state_in || !state_out || stride_bytes <= 0) return PPL_EINVAL;
-  const bool fused = stride_bytes % 16 == 0 && stride_bytes <= 1024 &&
+  const bool fused = stride_bytes % 4 == 0 && stride_bytes <= 1024 &&
                      ((reinterpret_cast<uintptr_t>(state_in) |
-                       reinterpret_cast<uintptr_t>(state_out)) & 15) == 0;
+                       reinterpret_cast<uintptr_t>(state_out)) & 3) == 0;
   if (fused)
     return resample_impl(lw, nullptr, max_lw_dev, n, m, seed, instance, t, ancestors, ws,
                          ws_bytes, stream, state_in, stride_bytes, state_out);
@@ -391,10 +391,11 @@ ppl_status ppl_smc_step(const ppl_model* model, float y_t, int32_t t, uint64_t s
   PPL_TRY(reset_ws(w, true, s));
   PPL_TRY(cuda_status(launch_smc_propagate(p, y_t, t, seed, x, lw, n, logz_acc, resampled,
                                            logz_est, w.hdr(), w.partials(), s)));
+  // resampling with the states' gather fused (4-byte records)
   PPL_TRY(cuda_status(launch_resample_coop(lw, nullptr, nullptr, n, n, seed, 0, (uint32_t)t,
                                            w.hdr(), w.tiles(), reinterpret_cast<char*>(w.prefix()),
-                                           w.l.bounds - w.l.prefix, anc, gate, s)));
-  PPL_TRY(cuda_status(launch_gather(x, n, sizeof(float), anc, n, x_tmp, gate, s)));
+                                           w.l.bounds - w.l.prefix, anc, gate, s, x,
+                                           (int64_t)sizeof(float), x_tmp)));
   PPL_TRY(cuda_status(launch_smc_commit(x, x_tmp, lw, n, gate, s)));
   return PPL_OK;
 }

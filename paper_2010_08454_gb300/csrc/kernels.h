@@ -85,7 +85,8 @@ cudaError_t launch_smc_propagate(const LgssmParams& p, float y_t, int32_t t, uin
 size_t smc_run_workspace(int64_t N, int64_t T);
 // Systematic resampling in one cooperative kernel: the ancestors, and with
 // rec_in the gathered records too (rec_out[k] = rec_in[anc[k]], rec_bytes a
-// multiple of 16 up to 1024, both pointers 16-byte aligned).  `barrier` holds
+// multiple of 4 up to 1024, both pointers 4-byte aligned; copied in 16-byte
+// words when size and pointers allow).  `barrier` holds
 // the grid barrier's words (resample_coop_barrier_bytes(), 128-byte aligned,
 // zeroed by the caller before the launch); `scratch` the per-chunk tables
 // (resample_coop_scratch(n) bytes, 16-byte aligned).

@@ -64,30 +64,44 @@ struct RcArgs {
   int64_t* kfirst;  // [n_chunks + 1] first output of each chunk (K_c), K_last = m
   int64_t* ioff;    // [n_chunks + 1] first work item of each chunk
   // fused gather (rec_words > 0): rec_out[k] = rec_in[a_k], records of
-  // rec_words 16-byte words, rec_in holding the n particles' records
-  const uint4* rec_in;
-  uint4* rec_out;
+  // rec_words words of 16 bytes (or of 4 bytes when rec_word4), rec_in
+  // holding the n particles' records
+  const void* rec_in;
+  void* rec_out;
   int32_t rec_words;
+  int32_t rec_word4;
 };
 
 // The records of outputs k0 .. k0 + nB - 1 of an item, by one warp: output j
 // copies the record of ancestor anc_of(j); consecutive lanes take consecutive
-// 16-byte words, so both the loads (ancestors are non-decreasing) and the
-// stores are coalesced.
-template <class AncOf>
-__device__ __forceinline__ void gather_item(const RcArgs& a, int64_t k0, int nB, AncOf anc_of,
-                                            int lane) {
-  const int W = a.rec_words;
+// words, so both the loads (ancestors are non-decreasing) and the stores are
+// coalesced.
+template <typename V, class AncOf>
+__device__ __forceinline__ void gather_words(const V* in, V* out_all, int W, int64_t k0, int nB,
+                                             AncOf anc_of, int lane) {
   const int total = nB * W;
-  uint4* out = a.rec_out + k0 * W;
-  if (W == 2) {
-    for (int e = lane; e < total; e += 32) out[e] = a.rec_in[(int64_t)anc_of(e >> 1) * 2 + (e & 1)];
+  V* out = out_all + k0 * W;
+  if (W == 1) {
+    for (int e = lane; e < total; e += 32) out[e] = in[anc_of(e)];
+  } else if (W == 2) {
+    for (int e = lane; e < total; e += 32) out[e] = in[(int64_t)anc_of(e >> 1) * 2 + (e & 1)];
   } else {
     for (int e = lane; e < total; e += 32) {
       const int j = e / W;
-      out[e] = a.rec_in[(int64_t)anc_of(j) * W + (e - j * W)];
+      out[e] = in[(int64_t)anc_of(j) * W + (e - j * W)];
     }
   }
+}
+
+template <class AncOf>
+__device__ __forceinline__ void gather_item(const RcArgs& a, int64_t k0, int nB, AncOf anc_of,
+                                            int lane) {
+  if (a.rec_word4)
+    gather_words(reinterpret_cast<const uint32_t*>(a.rec_in), reinterpret_cast<uint32_t*>(a.rec_out),
+                 a.rec_words, k0, nB, anc_of, lane);
+  else
+    gather_words(reinterpret_cast<const uint4*>(a.rec_in), reinterpret_cast<uint4*>(a.rec_out),
+                 a.rec_words, k0, nB, anc_of, lane);
 }
 
 // The weights of one thread's kRcItems particles from `base`: FP32
@@ -548,14 +562,17 @@ cudaError_t launch_resample_coop(const float* lw, const uint64_t* q_fixed, const
   a.anc = anc;
   a.gate = gate;
   a.n_chunks = (n + kRcChunk - 1) / kRcChunk;
-  a.rec_in = reinterpret_cast<const uint4*>(rec_in);
-  a.rec_out = reinterpret_cast<uint4*>(rec_out);
+  a.rec_in = rec_in;
+  a.rec_out = rec_out;
   a.rec_words = 0;
+  a.rec_word4 = 0;
   if (rec_in) {
-    if (!rec_out || rec_bytes <= 0 || rec_bytes % 16 || rec_bytes / 16 > 64 ||
-        ((reinterpret_cast<uintptr_t>(rec_in) | reinterpret_cast<uintptr_t>(rec_out)) & 15))
+    const uintptr_t al = reinterpret_cast<uintptr_t>(rec_in) | reinterpret_cast<uintptr_t>(rec_out);
+    if (!rec_out || rec_bytes <= 0 || rec_bytes > 1024 || rec_bytes % 4 || (al & 3))
       return cudaErrorInvalidValue;
-    a.rec_words = (int32_t)(rec_bytes / 16);
+    const bool w16 = rec_bytes % 16 == 0 && (al & 15) == 0;
+    a.rec_word4 = w16 ? 0 : 1;
+    a.rec_words = (int32_t)(w16 ? rec_bytes / 16 : rec_bytes / 4);
   }
   size_t off = 0;
   auto take = [&](size_t bytes) {

@@ -118,14 +118,16 @@ def test_device_errors_are_reported(ppl):
 
 @pytest.mark.parametrize("kind", ["normal", "onehot", "sparse"])
 @pytest.mark.parametrize("N,M", [(1, 1), (4099, 4099), (100003, 100780), (262147, 70001)])
-@pytest.mark.parametrize("rec", ["f32x8", "f32x12", "i16x8", "f32x3"])
+@pytest.mark.parametrize("rec", ["f32x8", "f32x12", "i16x8", "f32x3", "f32x1", "i16x3"])
 def test_resample_gather_bit_exact(ppl, orc, kind, N, M, rec):
-    # 32-, 48- and 16-byte records take the fused path, 12-byte ones the
-    # separate gather; ancestors and records against the oracle, bit for bit
+    # 32-, 48- and 16-byte records take the fused path in 16-byte words, 12-
+    # and 4-byte ones in 4-byte words, 6-byte ones the separate gather;
+    # ancestors and records against the oracle, bit for bit
     import torch
     rng = np.random.default_rng(N + M)
     cols, dtype = {"f32x8": (8, np.float32), "f32x12": (12, np.float32),
-                   "i16x8": (8, np.int16), "f32x3": (3, np.float32)}[rec]
+                   "i16x8": (8, np.int16), "f32x3": (3, np.float32), "f32x1": (1, np.float32),
+                   "i16x3": (3, np.int16)}[rec]
     state = rng.integers(-30000, 30000, (N, cols)).astype(dtype)
     lw = synth.log_weights(N, 7 + N, kind)
     st, anc_ref = orc.resample_from_lw(lw, M, 13, 1, 3)
