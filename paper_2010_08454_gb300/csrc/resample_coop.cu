@@ -17,14 +17,17 @@
 //      independently: a warp finds the item's range of candidate ancestors by
 //      three 32-way probes of the index, and its lanes merge those prefix sums
 //      with the item's sorted positions (merge path: Green, McColl, Bader, "GPU
-//      merge path", ICS 2012), one equal slice of the merge per lane.
+//      merge path", ICS 2012), one equal slice of the merge per lane; an item
+//      whose outputs all have one ancestor is filled directly.  With a record
+//      buffer the warp then copies its outputs' records (the fused gather).
 //
 // Every item costs at most 4096 weights and 256 outputs whatever the weights
 // are: a chunk holding most of the mass (degenerate importance weights)
 // becomes many items on many blocks and warps, with no block barrier between
 // them.  The ancestors are those of the scan-and-search path bit for bit (both
 // are exact integer computations of the same definition).  Traffic: lw twice
-// (the second time from L2), the ancestors once.
+// (the second time from L2), the ancestors once, and with the gather every
+// output's record once plus each distinct ancestor's record.
 #include <algorithm>
 
 #include "gridsync.cuh"
