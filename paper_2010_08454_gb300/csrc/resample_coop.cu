@@ -46,7 +46,7 @@ constexpr int kRcBatch = 32;                          // chunks summed between b
 // items; every chunk with outputs is charged it in the partition of the
 // items over the blocks, so that a block whose run crosses many sparsely
 // used chunks takes correspondingly fewer items.
-constexpr int kRcPrefixCost = 64;
+constexpr int kRcPrefixCost = 128;
 constexpr int kRcJobBlk = 8;     // chunk totals the layout job's first pass loads at once per thread
 constexpr int kRcJobPer = 4;     // chunks per thread in a tile of the layout job
 constexpr int kRcJobTile = kRcTpb * kRcJobPer;
