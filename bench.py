@@ -206,6 +206,26 @@ def _event_ms(torch, fn, reps):
     return e0.elapsed_time(e1) / reps
 
 
+def _device_ms(torch, fn, reps, flush=None):
+    """Median device time of one call of fn: all calls are enqueued behind a
+    device-side sleep, so the host's launch path never leaves the GPU idle
+    between a call's two events; the L2 is flushed before every call, outside
+    its events."""
+    s = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(reps)]
+    torch.cuda.synchronize()
+    torch.cuda._sleep(int(2e6 + reps * 4e5))  # ~1 ms + 0.2 ms per call at 2 GHz
+    for k in range(reps):
+        if flush is not None:
+            flush.fill_(k & 0xFF)
+        ev[k][0].record(s)
+        fn()
+        ev[k][1].record(s)
+    torch.cuda.synchronize()
+    return float(statistics.median(a.elapsed_time(b) for a, b in ev))
+
+
 def bench_smc(torch, ppl, reps=5):
     """Bootstrap filter on the linear-Gaussian model, T = 200, 2^20 particles: one persistent
     kernel, with the step-by-step path (one CUDA graph of 200 steps) timed beside it."""
@@ -322,11 +342,7 @@ def bench_normalise(torch, ppl, reps=20):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     for _ in range(3):
         ppl.ppl_logsumexp(lw, out=out, ws=ws)
-    t = []
-    for _ in range(reps):
-        flush.fill_(1)
-        t.append(_event_ms(torch, lambda: ppl.ppl_logsumexp(lw, out=out, ws=ws), 1))
-    ms = float(np.median(t))
+    ms = _device_ms(torch, lambda: ppl.ppl_logsumexp(lw, out=out, ws=ws), reps, flush)
     gbs = N * 4 / (ms / 1e3) / 1e9
     peak = (load_peaks() or {}).get("hbm_gbs")
     return {"workload": "log-sum-exp, ESS, max and argmax of 2^24 FP32 log-weights "

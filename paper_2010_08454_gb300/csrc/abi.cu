@@ -145,9 +145,16 @@ ppl_status ppl_infer_is_instance(const ppl_model* model, const ppl_data* data,
   cudaStream_t s = (cudaStream_t)stream;
   PPL_TRY(reset_ws(w, false, s));
   PPL_TRY(cuda_status(cudaMemsetAsync(out_dev, 0, sizeof(ppl_is_result), s)));
-  PPL_TRY(cuda_status(launch_poly_trace(p, data->x, data->y, data->len, n_particles, seed,
-                                        instance, lw_out, particles_out, w.hdr(), w.partials(),
-                                        out_dev, s)));
+  // the polynomial evaluations on the tensor cores while the data set fits in
+  // shared memory, in FP32 on the CUDA cores beyond
+  if (data->len <= trace_tc_max_points())
+    PPL_TRY(cuda_status(launch_poly_trace_tc(p, data->x, data->y, data->len, n_particles, seed,
+                                             instance, lw_out, particles_out, w.hdr(),
+                                             w.partials(), out_dev, s)));
+  else
+    PPL_TRY(cuda_status(launch_poly_trace(p, data->x, data->y, data->len, n_particles, seed,
+                                          instance, lw_out, particles_out, w.hdr(), w.partials(),
+                                          out_dev, s)));
   return PPL_OK;
 }
 

@@ -12,58 +12,6 @@
 namespace ppl {
 
 // ---------------------------------------------------------------------------
-// Final merge of the per-block partials, by the last block: warp k merges
-// degree k's partials (FP32, a lane-strided chain then a shuffle tree); the
-// sums S, S2 are recombined in FP64 around the merged maximum; thread 0
-// writes the summary.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void finalize_partials(const DegPartial* parts, int G, int n_deg,
-                                                  int min_deg, int64_t N, WsHeader* hdr,
-                                                  ppl_is_result* res) {
-  __shared__ DegPartial fin[kMaxDegrees];
-  __shared__ double fS[kMaxDegrees], fS2[kMaxDegrees];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (warp < kMaxDegrees) {
-    DegPartial a;
-    deg_empty(a);
-    for (int b = lane; b < G; b += 32) deg_merge(a, parts[b * kMaxDegrees + warp]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const DegPartial other = deg_shfl_xor(a, o);
-      deg_merge(a, other);
-    }
-    const float M = a.m;
-    double s = 0.0, s2 = 0.0;
-    if (M != -INFINITY) {
-      for (int b = lane; b < G; b += 32) {
-        const DegPartial& q = parts[b * kMaxDegrees + warp];
-        if (q.m == -INFINITY) continue;
-        const double e = (double)expf(q.m - M);
-        s += (double)q.S * e;
-        s2 += (double)q.S2 * e * e;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s += __shfl_xor_sync(0xffffffffu, s, o);
-      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    }
-    if (lane == 0) {
-      fin[warp] = a;
-      fS[warp] = s;
-      fS2[warp] = s2;
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    bool any = false;
-    for (int k = 0; k < n_deg; ++k) any |= fin[k].m != -INFINITY;
-    if (!any) record_status(&hdr->status, PPL_EEMPTY);
-    if (res) write_summary(fin, fS, fS2, n_deg, min_deg, N, ld_volatile_i32(&hdr->status), res);
-  }
-}
-
-// ---------------------------------------------------------------------------
 // Trace kernel: a persistent grid; each block runs groups of kTpb * PPT traces
 // (trace_group: draw, sort by degree, degree-specialised Horner, per-degree
 // partials) and merges the groups' partials into its running partial; the
@@ -119,80 +67,324 @@ __global__ void __launch_bounds__(kTpb, 4) poly_trace_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// Statistics pass over an existing set of log-weights (lw NULL = all 0).
+// Statistics pass over an existing set of log-weights (§3.6.2: the maximum,
+// log-sum-exp and ESS that normalise them), one read of lw at HBM speed.
+//
+// The 16-byte-aligned body of lw is cut into one contiguous range of float4
+// vectors per block (balanced to a 128-byte line); a block walks its range in
+// tiles of kTpb * kStatU vectors, each thread loading kStatU vectors of the
+// next tile while it folds the current one into its running statistics.  The
+// (at most three) elements before the first 16-byte boundary go to block 0
+// before its range, the (at most three) after the last whole vector to the
+// last block after its range, so every thread sees increasing indices.  The
+// last block to finish merges the blocks' partials.
 // ---------------------------------------------------------------------------
-constexpr int kStatVec = 4;  // float4 loads per thread per round: 16 log-weights in flight
+constexpr int kStatThreads = 256;                 // threads per block
+constexpr int kStatU = 4;                         // vectors per thread per tile
+constexpr int kStatTile = kStatThreads * kStatU;  // vectors per tile
+constexpr int kStatBlocksPerSm = 4;
+constexpr float kLog2e = 0x1.715476p+0f;
 
-// A thread's batch of log-weights (lowest index first) folded into its running
-// statistics: the batch maximum (lowest index on ties) rescales the sums once,
-// then every finite weight adds exp(lw - m) and its square; NaNs only raise the
-// flag.  Indices increase from batch to batch, so ties keep the earlier index.
-template <int B>
-__device__ __forceinline__ void add_batch(StatAcc& acc, const float (&v)[B], int64_t i0,
-                                          int64_t step) {
-  float mb = -INFINITY;
-  int64_t ib = 0x7fffffff;
-#pragma unroll
-  for (int j = 0; j < B; ++j) {
-    acc.nan |= v[j] != v[j];
-    if (v[j] > mb) {
-      mb = v[j];
-      ib = i0 + (j / 4) * step + (j % 4);
+// 2^t by the SFU's base-2 exponential (PTX ex2.approx.ftz: relative error
+// about 2^-22, results below 2^-126 flushed to zero, ex2(-inf) = 0).
+__device__ __forceinline__ float ex2_sfu(float t) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(t));
+  return r;
+}
+
+// Running statistics of one thread: maximum m and its (lowest) index, the
+// sums of exp(lw - m) and exp(2 (lw - m)), and a NaN flag.
+struct LseAcc {
+  float m, s, s2;
+  int arg, nan;
+  __device__ __forceinline__ void init() {
+    m = -INFINITY;
+    s = 0.0f;
+    s2 = 0.0f;
+    arg = 0x7fffffff;
+    nan = 0;
+  }
+  // one weight, at an index above every index added before
+  __device__ __forceinline__ void add(float v, int i) {
+    if (v != v) {
+      nan = 1;
+      return;
+    }
+    if (v > m) {
+      const float e = (m == -INFINITY) ? 0.0f : ex2_sfu((m - v) * kLog2e);
+      s *= e;
+      s2 *= e * e;
+      m = v;
+      arg = i;
+    }
+    if (m > -INFINITY) {
+      const float e = ex2_sfu((v - m) * kLog2e);
+      s += e;
+      s2 = fmaf(e, e, s2);
     }
   }
+};
+
+// A thread's tile folded into its running statistics.  The tile maximum
+// (maxNum: NaNs are passed over) is found first; only when it raises the
+// running maximum are the tile's values searched for its lowest index and the
+// sums rescaled, which after the first tiles is rare.  Every weight then adds
+// 2^((lw - m) log2 e) and its square: -inf adds exactly 0, and a NaN (or
+// +inf) poisons the tile's sum, whose tile is then summed again with those
+// values left out and the flag raised.  Slot j of the tile holds element
+// indices i0 + 4 kStatThreads j + 0..3.
+__device__ __forceinline__ void add_tile(LseAcc& acc, const float4 (&t)[kStatU], int64_t i0) {
+  float mb = -INFINITY;
+#pragma unroll
+  for (int j = 0; j < kStatU; ++j)
+    mb = fmaxf(mb, fmaxf(fmaxf(t[j].x, t[j].y), fmaxf(t[j].z, t[j].w)));
   if (mb > acc.m) {
-    const float e = (acc.m == -INFINITY) ? 0.0f : expf(acc.m - mb);
+    int c = 0;
+#pragma unroll
+    for (int j = kStatU - 1; j >= 0; --j) {  // the last match written is the lowest index
+      if (t[j].w == mb) c = 4 * j + 3;
+      if (t[j].z == mb) c = 4 * j + 2;
+      if (t[j].y == mb) c = 4 * j + 1;
+      if (t[j].x == mb) c = 4 * j;
+    }
+    const float e = (acc.m == -INFINITY) ? 0.0f : ex2_sfu((acc.m - mb) * kLog2e);
     acc.s *= e;
     acc.s2 *= e * e;
     acc.m = mb;
-    acc.arg = (int)ib;
+    acc.arg = (int)(i0 + (int64_t)(c >> 2) * 4 * kStatThreads + (c & 3));
   }
   if (acc.m > -INFINITY) {
+    const float m = acc.m;
+    float s = 0.0f, s2 = 0.0f;
 #pragma unroll
-    for (int j = 0; j < B; ++j) {
-      if (v[j] > -INFINITY) {  // NaN and -inf add nothing
-        const float e = expf(v[j] - acc.m);
-        acc.s += e;
-        acc.s2 = fmaf(e, e, acc.s2);
+    for (int j = 0; j < kStatU; ++j) {
+      const float v[4] = {t[j].x, t[j].y, t[j].z, t[j].w};
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const float e = ex2_sfu((v[c] - m) * kLog2e);
+        s += e;
+        s2 = fmaf(e, e, s2);
       }
+    }
+    if (s != s) {  // a NaN or +inf in the tile
+      acc.nan = 1;
+      s = 0.0f;
+      s2 = 0.0f;
+#pragma unroll
+      for (int j = 0; j < kStatU; ++j) {
+        const float v[4] = {t[j].x, t[j].y, t[j].z, t[j].w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          const float d = v[c] - m;
+          if (d == d) {
+            const float e = ex2_sfu(d * kLog2e);
+            s += e;
+            s2 = fmaf(e, e, s2);
+          }
+        }
+      }
+    }
+    acc.s += s;
+    acc.s2 += s2;
+  } else {  // nothing finite so far: the tile holds only -inf and NaN
+#pragma unroll
+    for (int j = 0; j < kStatU; ++j)
+      acc.nan |= (t[j].x != t[j].x) | (t[j].y != t[j].y) | (t[j].z != t[j].z) | (t[j].w != t[j].w);
+  }
+}
+
+// a <- merge(a, b); ties of the maximum keep the lower index
+__device__ __forceinline__ void lse_merge(LseAcc& a, const LseAcc& b) {
+  const float M = fmaxf(a.m, b.m);
+  if (M > -INFINITY) {
+    const float ea = (a.m == -INFINITY) ? 0.0f : ex2_sfu((a.m - M) * kLog2e);
+    const float eb = (b.m == -INFINITY) ? 0.0f : ex2_sfu((b.m - M) * kLog2e);
+    a.s = fmaf(a.s, ea, b.s * eb);
+    a.s2 = fmaf(a.s2, ea * ea, b.s2 * eb * eb);
+  }
+  if (b.m > a.m || (b.m == a.m && b.arg < a.arg)) a.arg = b.arg;
+  a.m = M;
+  a.nan |= b.nan;
+}
+
+__device__ __forceinline__ LseAcc lse_shfl_xor(const LseAcc& a, int o) {
+  LseAcc r;
+  r.m = __shfl_xor_sync(0xffffffffu, a.m, o);
+  r.s = __shfl_xor_sync(0xffffffffu, a.s, o);
+  r.s2 = __shfl_xor_sync(0xffffffffu, a.s2, o);
+  r.arg = __shfl_xor_sync(0xffffffffu, a.arg, o);
+  r.nan = __shfl_xor_sync(0xffffffffu, a.nan, o);
+  return r;
+}
+
+// Block merge of the threads' statistics; the result is valid in thread 0.
+__device__ __forceinline__ LseAcc lse_block_reduce(LseAcc a) {
+  __shared__ LseAcc slots[kStatThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lse_merge(a, lse_shfl_xor(a, o));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) slots[warp] = a;
+  __syncthreads();
+  if (warp == 0) {
+    LseAcc r;
+    r.init();
+    if (lane < kStatThreads / 32) r = slots[lane];
+#pragma unroll
+    for (int o = kStatThreads / 64; o > 0; o >>= 1) lse_merge(r, lse_shfl_xor(r, o));
+    a = r;
+  }
+  return a;
+}
+
+// Double-float accumulation (Knuth's TwoSum: hi + lo carries the exact sum
+// of the FP32 terms added so far, to about 48 bits).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float v) {
+  const float s = hi + v;
+  const float bp = s - hi;
+  const float err = (hi - (s - bp)) + (v - bp);
+  hi = s;
+  lo += err;
+}
+
+// Final merge by the last block: the maximum and its lowest index in FP32
+// (exact), then every partial's sums rescaled to the merged maximum (FP32
+// exp of a difference of two floats) and added in double-float per lane,
+// combined across lanes and warps in FP64; thread 0 writes the results.
+__device__ __forceinline__ void lse_finalize(const StatPartial* parts, int G, int64_t N,
+                                             WsHeader* hdr, double* lse_out) {
+  __shared__ float M_sh;
+  __shared__ double wsum[kStatThreads / 32][2];
+  LseAcc a;
+  a.init();
+  for (int b = threadIdx.x; b < G; b += kStatThreads) {
+    const StatPartial p = parts[b];
+    LseAcc o;
+    o.m = p.m;
+    o.s = p.s;
+    o.s2 = p.s2;
+    o.arg = p.arg;
+    o.nan = p.nan;
+    lse_merge(a, o);
+  }
+  const LseAcc r = lse_block_reduce(a);
+  if (threadIdx.x == 0) M_sh = r.m;
+  __syncthreads();
+  const float M = M_sh;
+  float sh = 0.0f, sl = 0.0f, qh = 0.0f, ql = 0.0f;
+  if (M > -INFINITY) {
+    for (int b = threadIdx.x; b < G; b += kStatThreads) {
+      const float pm = parts[b].m;
+      if (pm == -INFINITY) continue;
+      const float e = ex2_sfu((pm - M) * kLog2e);
+      df_add(sh, sl, parts[b].s * e);
+      df_add(qh, ql, parts[b].s2 * e * e);
+    }
+  }
+  double s = (double)sh + (double)sl, s2 = (double)qh + (double)ql;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    wsum[warp][0] = s;
+    wsum[warp][1] = s2;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    s = 0.0;
+    s2 = 0.0;
+#pragma unroll
+    for (int w = 0; w < kStatThreads / 32; ++w) {
+      s += wsum[w][0];
+      s2 += wsum[w][1];
+    }
+    int32_t code = 0;
+    if (r.nan) code = PPL_ENAN;
+    else if (!(M > -INFINITY)) code = PPL_EEMPTY;
+    if (code) record_status(&hdr->status, code);
+    const double lse = (double)M + log(s);
+    const double ess = s * s / s2;
+    hdr->max_lw = M;
+    hdr->lse = lse;
+    hdr->ess = ess;
+    hdr->argmax = r.arg;
+    if (lse_out) {
+      lse_out[0] = lse;
+      lse_out[1] = ess;
+      lse_out[2] = (double)M;
+      lse_out[3] = (double)r.arg;
     }
   }
 }
 
-__global__ void __launch_bounds__(kTpb) stats_kernel(const float* __restrict__ lw, int64_t N,
-                                                     WsHeader* hdr, StatPartial* parts,
-                                                     double* lse_out) {
-  StatAcc acc;
-  acc.init();
-  const int64_t stride = (int64_t)gridDim.x * kTpb;
-  int64_t done = 0;  // the prefix handled by the vector loop
-  if (lw && (reinterpret_cast<uintptr_t>(lw) & 15) == 0) {
-    // coalesced 16-byte loads, kStatVec of them in flight per thread; thread t
-    // of the grid takes vectors t, t + stride, ..., kStatVec per round
-    const float4* v4 = reinterpret_cast<const float4*>(lw);
-    const int64_t n4 = N / 4;
-    const int64_t round = stride * kStatVec;
-    const int64_t full = n4 / round * round;  // vectors in whole rounds
-    for (int64_t q = (int64_t)blockIdx.x * kTpb + threadIdx.x; q < full; q += round) {
-      float v[4 * kStatVec];
+// Vectors [q0 + j kStatThreads + tid] of a whole tile (streamed: read once).
+__device__ __forceinline__ void load_tile(float4 (&t)[kStatU], const float4* __restrict__ v4) {
 #pragma unroll
-      for (int r = 0; r < kStatVec; ++r) {
-        const float4 x = __ldcs(v4 + q + r * stride);
-        v[4 * r] = x.x;
-        v[4 * r + 1] = x.y;
-        v[4 * r + 2] = x.z;
-        v[4 * r + 3] = x.w;
+  for (int j = 0; j < kStatU; ++j) t[j] = __ldcs(v4 + j * kStatThreads + threadIdx.x);
+}
+
+__global__ void __launch_bounds__(kStatThreads, kStatBlocksPerSm) stats_kernel(
+    const float* __restrict__ lw, int64_t N, WsHeader* hdr, StatPartial* parts,
+    double* lse_out) {
+  LseAcc acc;
+  acc.init();
+  const int tid = threadIdx.x;
+  const int G = gridDim.x, b = blockIdx.x;
+  const int64_t mis = (int64_t)(((16 - (reinterpret_cast<uintptr_t>(lw) & 15)) & 15) / 4);
+  const int head = (int)(mis < N ? mis : N);
+  const int64_t n4 = (N - head) / 4;
+  const int tail = (int)(N - head - 4 * n4);
+  if (b == 0 && tid < head) acc.add(lw[tid], tid);
+  // this block's vectors [begin, end), cut at multiples of 8 (128 bytes)
+  const int64_t lines = (n4 + 7) / 8;
+  const int64_t begin = ::min(n4, lines * b / G * 8);
+  const int64_t end = ::min(n4, lines * (b + 1) / G * 8);
+  const float4* v4 = reinterpret_cast<const float4*>(lw + head) + begin;
+  const int n_vec = (int)(end - begin);
+  const int full = n_vec / kStatTile * kStatTile;  // vectors in whole tiles
+  const int64_t i_base = head + 4 * (begin + tid);  // element index of slot 0, tile 0
+  if (full > 0) {
+    float4 cur[kStatU];
+    load_tile(cur, v4);
+    for (int q0 = 0; q0 < full; q0 += kStatTile) {
+      float4 nxt[kStatU];
+      const bool more = q0 + kStatTile < full;  // the same for the whole block
+      if (more) load_tile(nxt, v4 + q0 + kStatTile);
+      add_tile(acc, cur, i_base + 4 * (int64_t)q0);
+      if (more) {
+#pragma unroll
+        for (int j = 0; j < kStatU; ++j) cur[j] = nxt[j];
       }
-      add_batch<4 * kStatVec>(acc, v, 4 * q, 4 * stride);
     }
-    done = 4 * full;
   }
-  for (int64_t i = done + (int64_t)blockIdx.x * kTpb + threadIdx.x; i < N; i += stride)
-    acc.add(lw ? lw[i] : 0.0f, (int)i, -1);
-  StatAcc r = block_reduce_stat(acc);
-  if (threadIdx.x == 0) to_partial(r, parts + blockIdx.x);
-  if (elect_last_block(&hdr->ticket[0]))
-    finalize_stats(parts, gridDim.x, N, nullptr, hdr, nullptr, lse_out);
+  if (full < n_vec) {  // the range's last, partial tile
+    float4 t[kStatU];
+#pragma unroll
+    for (int j = 0; j < kStatU; ++j) {
+      const int q = full + j * kStatThreads + tid;
+      t[j] = q < n_vec ? __ldcs(v4 + q)
+                       : make_float4(-INFINITY, -INFINITY, -INFINITY, -INFINITY);
+    }
+    add_tile(acc, t, i_base + 4 * (int64_t)full);
+  }
+  if (b == G - 1 && tid < tail) {
+    const int64_t i = head + 4 * n4 + tid;
+    acc.add(lw[i], (int)i);
+  }
+  const LseAcc r = lse_block_reduce(acc);
+  if (tid == 0) {
+    StatPartial p;
+    p.m = r.m;
+    p.s = r.s;
+    p.s2 = r.s2;
+    p.arg = r.arg;
+    p.nan = r.nan;
+    parts[b] = p;
+  }
+  if (elect_last_block(&hdr->ticket[0])) lse_finalize(parts, G, N, hdr, lse_out);
 }
 
 // ---------------------------------------------------------------------------
@@ -312,7 +504,11 @@ cudaError_t launch_poly_trace(const PolyParams& p, const float* x, const float* 
 
 cudaError_t launch_stats(const float* lw, int64_t N, WsHeader* hdr, void* parts,
                          double* lse_out, cudaStream_t s) {
-  stats_kernel<<<stream_grid(N), kTpb, 0, s>>>(lw, N, hdr, (StatPartial*)parts, lse_out);
+  // a few tiles per block at least; up to kStatBlocksPerSm blocks per SM
+  const int64_t tiles = (N / 4 + kStatTile - 1) / kStatTile;
+  const int grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>((tiles + 1) / 2, (int64_t)num_sms() * kStatBlocksPerSm));
+  stats_kernel<<<grid, kStatThreads, 0, s>>>(lw, N, hdr, (StatPartial*)parts, lse_out);
   return cudaGetLastError();
 }
 

@@ -24,6 +24,13 @@ cudaError_t launch_poly_trace(const PolyParams& p, const float* x, const float* 
                               int64_t N, uint64_t seed, uint32_t instance, float* lw_out,
                               ppl_poly_particle* rec_out, WsHeader* hdr, void* parts,
                               ppl_is_result* res, cudaStream_t s, const void* suff = nullptr);
+// trace_tc.cu: the same pass with the factor's polynomial evaluations on the
+// tensor cores (data sets of up to trace_tc_max_points() points).
+int trace_tc_max_points();
+cudaError_t launch_poly_trace_tc(const PolyParams& p, const float* x, const float* y, int64_t L,
+                                 int64_t N, uint64_t seed, uint32_t instance, float* lw_out,
+                                 ppl_poly_particle* rec_out, WsHeader* hdr, void* parts,
+                                 ppl_is_result* res, cudaStream_t s);
 // Sufficient statistics of a data set for the line-fitting factor (one
 // block); `out` holds suffstat_bytes() bytes, 16-byte aligned.
 size_t suffstat_bytes();

@@ -284,4 +284,57 @@ __device__ __forceinline__ void write_summary(const DegPartial (&p)[kMaxDegrees]
   res->status = status;
 }
 
+// ---------------------------------------------------------------------------
+// Final merge of the per-block partials, by the last block: warp k merges
+// degree k's partials (FP32, a lane-strided chain then a shuffle tree); the
+// sums S, S2 are recombined in FP64 around the merged maximum; thread 0
+// writes the summary.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void finalize_partials(const DegPartial* parts, int G, int n_deg,
+                                                  int min_deg, int64_t N, WsHeader* hdr,
+                                                  ppl_is_result* res) {
+  __shared__ DegPartial fin[kMaxDegrees];
+  __shared__ double fS[kMaxDegrees], fS2[kMaxDegrees];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp < kMaxDegrees) {
+    DegPartial a;
+    deg_empty(a);
+    for (int b = lane; b < G; b += 32) deg_merge(a, parts[b * kMaxDegrees + warp]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const DegPartial other = deg_shfl_xor(a, o);
+      deg_merge(a, other);
+    }
+    const float M = a.m;
+    double s = 0.0, s2 = 0.0;
+    if (M != -INFINITY) {
+      for (int b = lane; b < G; b += 32) {
+        const DegPartial& q = parts[b * kMaxDegrees + warp];
+        if (q.m == -INFINITY) continue;
+        const double e = (double)expf(q.m - M);
+        s += (double)q.S * e;
+        s2 += (double)q.S2 * e * e;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+      fin[warp] = a;
+      fS[warp] = s;
+      fS2[warp] = s2;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bool any = false;
+    for (int k = 0; k < n_deg; ++k) any |= fin[k].m != -INFINITY;
+    if (!any) record_status(&hdr->status, PPL_EEMPTY);
+    if (res) write_summary(fin, fS, fS2, n_deg, min_deg, N, ld_volatile_i32(&hdr->status), res);
+  }
+}
+
+
 }  // namespace ppl

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import load_ppl
+from gpu_util import check_summary, load_ppl
 
 pytestmark = pytest.mark.gpu
 
@@ -34,9 +34,7 @@ def _check_instances(orc, inst, results, seed, which):
         tol = 1e-3 + 2.0 ** -21 * abs(ref["max_lw"])  # 4 FP32 ulps of the largest lw
         assert abs(r["log_z"] - ref["log_z"]) <= tol, (b, r["log_z"], ref["log_z"])
         assert r["ess"] == pytest.approx(ref["ess"], rel=1e-3)
-        assert np.allclose(r["p_n"], ref["p_n"], rtol=1e-4, atol=1e-12), b
-        s = np.max(np.abs(ref["mean_c"])) + 1e-12
-        assert np.allclose(r["mean_c"], ref["mean_c"], rtol=1e-4, atol=1e-5 * s), b
+        check_summary(r, ref, b)
         if r["argmax"] != ref["argmax"]:
             assert abs(r["max_lw"] - ref["max_lw"]) <= tol
 
@@ -83,3 +81,31 @@ def test_graph_replay_and_autotune_cache(ppl, orc, tmp_path):
     torch.cuda.synchronize()
     res = ppl.read_batch_results(out, 300)
     _check_instances(orc, inst, res, 5, list(range(0, 300, 23)) + [299])
+
+
+def test_batched_4096_instances_sampled_against_oracle(ppl, orc, tmp_path):
+    # the benchmarked shape itself: 4096 instances, data lengths log-uniform in
+    # [16, 4096], particle counts log-uniform in [2^10, 2^16], one autotuned
+    # launch; 48 instances checked against the oracle: the eight largest N x L,
+    # the largest N (tens of tiles, where the running maxima of earlier tiles
+    # decide which traces later tiles skip), the largest and
+    # smallest L, the smallest N, and a seeded draw of the rest
+    inst = synth.batched_instances(4096, 3)
+    x, y, doff, poff = _device_batch(ppl, inst)
+    model = ppl.poly_model()
+    ws = ppl.batched_workspace(inst["data_off"], inst["part_off"])
+    out = ppl.batch_results_tensor(4096)
+    plan = ppl.ppl_batched_autotune(model, x, y, doff, poff, inst["data_off"], inst["part_off"],
+                                    3, out, ws, str(tmp_path / "tune.json"))
+    out.zero_()
+    ppl.ppl_infer_is_batched(model, x, y, doff, poff, 3, plan, out, ws)
+    assert ppl.ppl_batched_status(ws) == 0
+    res = ppl.read_batch_results(out, 4096)
+    N, L = inst["N"], inst["L"]
+    pick = {int(b) for b in np.argsort(N * L)[-8:]}
+    pick |= {int(np.argmax(N)), int(np.argmax(L)), int(np.argmin(L)), int(np.argmin(N))}
+    rest = np.setdiff1d(np.arange(4096), sorted(pick))
+    pick |= {int(b) for b in np.random.default_rng(48).choice(rest, 48 - len(pick), replace=False)}
+    pick = sorted(pick)
+    assert len(pick) == 48 and max(N[pick]) > 65000
+    _check_instances(orc, inst, res, 3, pick)

@@ -177,3 +177,38 @@ def test_bounded_wait_reports_timeout_and_recovers(ppl):
     ppl.ppl_resample(1000, 1, q_fixed=q, ancestors=anc, ws=ws)
     assert ppl.ppl_workspace_status(ws) == ppl.PPL_OK
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("source", ["linefitting", "normal"])
+def test_resample_gather_full_size_2_24(ppl, orc, source):
+    # the headline step's resampling at its own size: N = M = 2^24, 32-byte
+    # particle records, the maximum taken from the trace kernel's summary as
+    # in the timed step; "linefitting" resamples the trace kernel's own
+    # population (256 points, ESS near 1: most outputs share a few ancestors),
+    # "normal" a population with ESS near N/e (unit-variance log-weights: the
+    # merge path's many-ancestor case); ancestors and records bit for bit
+    import torch
+    N = 1 << 24
+    model = ppl.poly_model()
+    parts = ppl.poly_particles(N)
+    if source == "linefitting":
+        x, y = synth.poly_dataset(256, 1)
+        lw = torch.empty(N, dtype=torch.float32, device="cuda")
+        res = ppl.ppl_infer_is_instance(model, _t(x), _t(y), N, 1, 0, lw_out=lw,
+                                        particles_out=parts)
+        mx = ppl.result_max_lw(res)
+    else:
+        lw = _t(synth.log_weights(N, 21, "normal", scale=1.0))
+        rng = np.random.default_rng(5)
+        parts.copy_(torch.from_numpy(rng.standard_normal((N, 8)).astype(np.float32)))
+        mx = None
+    anc, out = ppl.ppl_resample_gather(N, 1, lw, parts, max_lw_dev=mx, instance=0, t=0)
+    lw_h, parts_h = lw.cpu().numpy(), parts.cpu().numpy()
+    st, anc_ref = orc.resample_from_lw(lw_h, N, 1, 0, 0)
+    assert st == 0
+    anc_h = anc.cpu().numpy()
+    assert np.array_equal(anc_h, anc_ref)
+    assert np.array_equal(out.cpu().numpy().view(np.uint32),
+                          orc.gather(parts_h, anc_ref).view(np.uint32))
+    if source == "normal":
+        assert len(np.unique(anc_h)) > N // 4  # many distinct ancestors

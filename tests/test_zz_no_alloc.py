@@ -20,6 +20,7 @@ def test_noalloc_resample_matches_workspace_resample_twice():
     lib = ppl.lib()
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     cases = [("lw", 262147, 262147, synth.log_weights(262147, 5, "normal", scale=4.0)),
+             ("lw", 262147, 100003, synth.log_weights(262147, 7, "sparse", scale=4.0)),
              ("q", 1 << 20, 777777, synth.fixed_weights(1 << 20, 6))]
     for call in range(2):
         for kind, n, m, data in cases:
@@ -36,6 +37,20 @@ def test_noalloc_resample_matches_workspace_resample_twice():
             assert st == ppl.PPL_OK
             assert lib.ppl_resample_noalloc_status(stream) == ppl.PPL_OK
             assert torch.equal(anc, ref), (call, kind)
+    # every weight zero: the device reports PPL_EEMPTY through the status call,
+    # and the next call, which clears the status word, reports PPL_OK again
+    dead = torch.full((5000,), float("-inf"), dtype=torch.float32, device="cuda")
+    anc = torch.empty(5000, dtype=torch.int32, device="cuda")
+    assert lib.ppl_resample_noalloc(ctypes.c_void_p(dead.data_ptr()), None, 5000, 5000,
+                                    ctypes.c_uint64(1), 0, 0, ctypes.c_void_p(anc.data_ptr()),
+                                    stream) == ppl.PPL_OK
+    assert lib.ppl_resample_noalloc_status(stream) == ppl.PPL_EEMPTY
+    live = torch.zeros(5000, dtype=torch.float32, device="cuda")
+    assert lib.ppl_resample_noalloc(ctypes.c_void_p(live.data_ptr()), None, 5000, 5000,
+                                    ctypes.c_uint64(1), 0, 0, ctypes.c_void_p(anc.data_ptr()),
+                                    stream) == ppl.PPL_OK
+    assert lib.ppl_resample_noalloc_status(stream) == ppl.PPL_OK
+    assert torch.equal(anc, ppl.ppl_resample(5000, 1, lw=live))
     # beyond the static scratch: rejected before any work
     big = torch.zeros((1 << 20) + 1, dtype=torch.float32, device="cuda")
     out = torch.empty(16, dtype=torch.int32, device="cuda")
