@@ -39,14 +39,33 @@ WORKLOAD = ("linefitting likelihood weighting, 2^24 particles x 256 points, degr
             "uniform{2..5}, coefficients N(0,10^2), sigma 0.5; + log-sum-exp/ESS + posterior "
             "reduce + systematic resampling (64-bit fixed point) + gather of 32-byte records")
 KERNELS_PER_STEP = 2  # trace (normalisation and posterior fused), resampling (gather fused)
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one
-# poly_trace_kernel launch on the default workload, from the full-size ncu
-# capture summarised in profiles/poly_trace_kernel_2e22x256.md; re-measure
-# whenever the kernel changes.
-TRACE_TRAFFIC_BYTES = 3329792 + 547968512
-# The same for the resampling kernel with the gather fused (profiles/
-# resample_coop_kernel_2e22.md); re-measure whenever the kernel changes.
-RG_TRAFFIC_BYTES = 67785472 + 542437120
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# each of the step's kernels on the default workload, from an ncu capture of
+# that kernel, with the SHA-256 prefix of the source file it was built from.
+# bench.py reports a figure only while the source still has that digest, so
+# a kernel changed since its capture reports traffic null instead of a stale
+# number.
+MEASURED_TRAFFIC = {
+    "poly_trace_tc_kernel": {"bytes": 163330 + 541910000, "source": "trace_tc.cu",
+                             "sha256": "df40aa9872af14d1"},
+    "resample_coop_kernel": {"bytes": 67370000 + 538910000, "source": "resample_coop.cu",
+                             "sha256": "2bcd3b331248d2cc"},
+}
+
+
+def measured_traffic(kernel):
+    """The captured DRAM bytes of `kernel`, or None when its source changed."""
+    import hashlib
+    ent = MEASURED_TRAFFIC.get(kernel)
+    if not ent or ent["bytes"] is None or ent["sha256"] is None:
+        return None
+    path = os.path.join(ROOT, "paper_2010_08454_gb300", "csrc", ent["source"])
+    try:
+        with open(path, "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return ent["bytes"] if digest == ent["sha256"] else None
 
 
 def parse():
@@ -62,7 +81,7 @@ def parse():
     ap.add_argument("--particles", type=int, default=N_PARTICLES,
                     help="particles per step (smaller cases for profiling only)")
     ap.add_argument("--config", choices=["smc", "batched", "learned", "suffstat", "small",
-                                         "normalise"],
+                                         "normalise", "linefitting_small", "resample_normal"],
                     help="run only this secondary workload and print its line (profiling)")
     return ap.parse_args()
 
@@ -289,6 +308,80 @@ def bench_smc(torch, ppl, reps=5):
                                # state gather fused, commit
                                "gpu_launches_per_filter": 3 * T,
                                "same_particles": bool(torch.equal(out["x"], x))}}
+
+
+def bench_linefitting_small(torch, ppl, replays=100):
+    """The paper's line-fitting example at its own size (Fig. 1, §1.1): 32
+    points from seed 0, 10^5 particles, inference seed 0; one call (trace,
+    normalisation, posterior) captured in a CUDA graph and replayed."""
+    import numpy as np
+
+    import synth
+    N, L = 100000, 32
+    x, y = synth.poly_dataset(L, 0)
+    xd, yd = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    model = ppl.poly_model()
+    ws = ppl.workspace(model, N, L)
+    res = ppl.result_tensor()
+    lw = torch.empty(N, dtype=torch.float32, device="cuda")
+    parts = ppl.poly_particles(N)
+
+    def call():
+        ppl.ppl_infer_is_instance(model, xd, yd, N, 0, 0, out=res, lw_out=lw, particles_out=parts,
+                                  ws=ws)
+    call()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    cs = torch.cuda.Stream()
+    with torch.cuda.graph(g, stream=cs):
+        call()
+    g.replay()
+    torch.cuda.synchronize()
+    ms = _event_ms(torch, g.replay, replays)
+    r = ppl.read_result(res)
+    return {"workload": "linefitting likelihood weighting, 32 points (data seed 0), 10^5 "
+                        "particles (seed 0), records and log-weights written; one graph replay "
+                        "per call, inputs resident (64 KB of data and 3.6 MB of outputs stay in L2)",
+            "metric": "particle-traces/sec", "value": N / (ms / 1e3), "unit": "traces/s",
+            "ms_per_call": ms, "replays": replays, "log_z": r["log_z"], "status": r["status"],
+            "gpu_launches_per_call": 1}
+
+
+def bench_resample_normal(torch, ppl, reps=20):
+    """The fused resampling + gather on a non-degenerate population: 2^24
+    unit-variance normal log-weights (ESS about N/e, so most outputs start a
+    new ancestor and the merge path does the work), 32-byte records, against
+    the measured HBM bandwidth; L2 flushed before every timed call."""
+    import numpy as np
+
+    import synth
+    N = 1 << 24
+    lw = torch.from_numpy(synth.log_weights(N, 21, "normal", scale=1.0)).cuda()
+    rec = torch.from_numpy(np.random.default_rng(5).standard_normal((N, 8)).astype(np.float32)).cuda()
+    out = torch.empty_like(rec)
+    anc = torch.empty(N, dtype=torch.int32, device="cuda")
+    ws = ppl.workspace(ppl.poly_model(), N, 0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def call():
+        ppl.ppl_resample_gather(N, 1, lw, rec, state_out=out, ancestors=anc, ws=ws)
+    for _ in range(3):
+        call()
+    ms = _device_ms(torch, call, reps, flush)
+    assert ppl.ppl_workspace_status(ws) == 0
+    distinct = int(torch.unique(anc).numel())
+    algo = N * (4 + 4 + 32) + distinct * 32
+    peak = (load_peaks() or {}).get("hbm_gbs")
+    gbs = algo / (ms / 1e3) / 1e9
+    return {"workload": "systematic resampling (64-bit fixed point) + gather of 32-byte records, "
+                        "2^24 particles, lw ~ N(0, 1) (ESS near N/e); the maximum found by the "
+                        "statistics pass inside the call",
+            "metric": "GB/s (algorithmic)", "value": gbs, "unit": "GB/s", "ms_per_call": ms,
+            "bytes_per_call": algo, "distinct_ancestors": distinct, "hbm_peak_gbs": peak,
+            "frac": gbs / peak if peak else None,
+            "work": "lw 4 B in, ancestor 4 B and record 32 B out per particle; each distinct "
+                    "ancestor's record in (the statistics pass re-reads lw: not counted)",
+            "gpu_launches_per_call": 2}
 
 
 def bench_suffstat(torch, ppl, reps=10):
@@ -578,12 +671,17 @@ def run_ours(args):
     summary = ppl.read_result(res)
     if status != 0 or summary["status"] != 0:
         raise RuntimeError(f"device status {status}/{summary['status']}")
-    # algorithmic FP32 work of the factor, from this population's sampled degrees:
-    # per particle and point, Horner (ncoef - 1 FMA) + residual (1 add) + square-accumulate (1 FMA)
+    # algorithmic work of the factor, from this population's sampled degrees.
+    # The trace kernel forms every residual y - f(x) as a product on the
+    # tensor cores: per trace and point, ncoef coefficient columns and the y
+    # column, each as three TF32 products (hi hi, hi lo, lo hi) for an
+    # FP32-accurate result.  The same factor on FP32 cores would take Horner
+    # (ncoef - 1 FMA) + residual (1 add) + square-accumulate (1 FMA).
     _, deg, _ = ppl.decode_particles(parts)
     counts = torch.bincount(deg.to(torch.int64) - 2, minlength=4).cpu().numpy()
     ncoef = np.arange(2, 6) + 1
-    flops_per_launch = float(N_POINTS * np.sum(counts * (2 * (ncoef - 1) + 1 + 2)))
+    tc_flops_per_launch = float(3 * 2 * N_POINTS * np.sum(counts * (ncoef + 1)))
+    fp32_flops_per_launch = float(N_POINTS * np.sum(counts * (2 * (ncoef - 1) + 1 + 2)))
 
     events = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     sampler = ClockSampler(gpu_index_for_smi(torch, local))
@@ -651,8 +749,13 @@ def run_ours(args):
     max_mhz = (peaks or {}).get("sm_max_mhz", 2070.0)
     # FP32 FMA peak: SMs x 128 lanes x 2 FLOP x max SM clock
     peak_tflops = sm_count * 128 * 2 * max_mhz * 1e6 / 1e12
+    # TF32 tensor peak: the measured BF16 burst figure x the nominal dense
+    # TF32 / BF16 ratio (1.1 / 2.25 PFLOP/s)
+    bf16 = (peaks or {}).get("bf16_tflops")
+    tf32_peak = (bf16 if bf16 else 1900.0) * 1.1 / 2.25
     trace_ms = float(stage[:, 0].mean())
-    achieved = flops_per_launch / (trace_ms / 1e3) / 1e12
+    achieved = tc_flops_per_launch / (trace_ms / 1e3) / 1e12
+    achieved_fp32 = fp32_flops_per_launch / (trace_ms / 1e3) / 1e12
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -661,12 +764,22 @@ def run_ours(args):
                        "2^24 particles", f"{N} particles"), "particles": N, "data_points": N_POINTS,
                    "data_seed": DATA_SEED, "seed": INFER_SEED, "parallelism": f"replicas{world}",
                    "l2": "flushed between timed steps (256 MiB write outside the events)"},
-        "roofline": {"kernel": "poly_trace_kernel", "bound": "alu", "achieved": achieved,
-                     "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved / peak_tflops,
-                     "traffic": TRACE_TRAFFIC_BYTES if N == N_PARTICLES else None,
+        "roofline": {"kernel": "poly_trace_tc_kernel", "bound": "tensor", "achieved": achieved,
+                     "peak": tf32_peak, "unit": "TFLOP/s", "frac": achieved / tf32_peak,
+                     "traffic": measured_traffic("poly_trace_tc_kernel")
+                     if N == N_PARTICLES else None,
                      "traffic_unit": "bytes per launch",
-                     "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {max_mhz} MHz",
-                     "work": "FP32 flops of the factor: L x (2 ncoef + 1) per trace"},
+                     "peak_source": ("TF32 dense: measured BF16 burst x 1.1/2.25 (nominal ratio), "
+                                     "of measured") if bf16 else "fallback BF16 x 1.1/2.25",
+                     "work": "TF32 flops of the residual products: 3 (split) x 2 x L x (ncoef + 1) "
+                             "per trace, from the sampled degrees",
+                     "timing": "CUDA events around ppl_infer_is_instance on its stream (two "
+                               "512-byte memsets and the trace kernel)"},
+        "roofline_fp32_equivalent": {
+            "kernel": "poly_trace_tc_kernel", "bound": "alu", "achieved": achieved_fp32,
+            "peak": peak_tflops, "unit": "TFLOP/s", "frac": achieved_fp32 / peak_tflops,
+            "peak_source": f"derived: {sm_count} SMs x 128 FP32 lanes x 2 x {max_mhz} MHz",
+            "work": "the factor as FP32 Horner would count it: L x (2 ncoef + 1) per trace"},
         "stages_ms": {"trace": trace_ms, "posterior": float(stage[:, 1].mean()),
                       "resample_gather": rg_ms},
         "roofline_resample_gather": {
@@ -676,7 +789,7 @@ def run_ours(args):
             "frac": rg_bytes / (rg_ms / 1e3) / 1e9 / (peaks or {}).get("hbm_gbs", 6800.0),
             "peak_source": "measured copy bandwidth" if peaks else "fallback",
             "bytes_per_step": rg_bytes, "distinct_ancestors": distinct,
-            "traffic": RG_TRAFFIC_BYTES if N == N_PARTICLES else None,
+            "traffic": measured_traffic("resample_coop_kernel") if N == N_PARTICLES else None,
             "traffic_unit": "bytes per launch",
             "work": "lw 4 B in, ancestor 4 B and record out per particle; each distinct "
                     "ancestor's record in"},
@@ -688,7 +801,9 @@ def run_ours(args):
         "wall_s": t_wall,
     }
     if not args.no_configs:
-        out["configs"] = {"smc_lgssm_T200_2e20": bench_smc(torch, ppl),
+        out["configs"] = {"linefitting_1e5x32": bench_linefitting_small(torch, ppl),
+                          "resample_gather_2e24_normal": bench_resample_normal(torch, ppl),
+                          "smc_lgssm_T200_2e20": bench_smc(torch, ppl),
                           "suffstat_linefitting_2e24x256": bench_suffstat(torch, ppl),
                           "small_models_2e24": bench_small_models(torch, ppl),
                           "normalise_2e24": bench_normalise(torch, ppl),
@@ -708,7 +823,8 @@ def run_config(args):
     ppl.lib()
     fn = {"smc": bench_smc, "batched": bench_batched, "learned": bench_learned,
           "suffstat": bench_suffstat, "small": bench_small_models,
-          "normalise": bench_normalise}[args.config]
+          "normalise": bench_normalise, "linefitting_small": bench_linefitting_small,
+          "resample_normal": bench_resample_normal}[args.config]
     print(json.dumps({"config": args.config, "result": fn(torch, ppl)}), flush=True)
     return 0
 

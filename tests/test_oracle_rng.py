@@ -40,7 +40,12 @@ print(json.dumps(o.numpy().view(np.uint32).astype(np.int64).tolist()))
 
 
 def test_philox_matches_triton_library(orc):
-    pytest.importorskip("triton")
+    # Triton's Philox is the one independent reference for the round function
+    # on this machine: without it the pin fails instead of vanishing as a skip
+    try:
+        import triton  # noqa: F401
+    except ImportError:
+        pytest.fail("triton is not importable: the independent Philox4x32-10 reference is missing")
     rng = np.random.default_rng(123)
     ctr = rng.integers(0, 2 ** 32, (16, 4), dtype=np.uint64).astype(np.uint32)
     key = rng.integers(0, 2 ** 32, (16, 2), dtype=np.uint64).astype(np.uint32)
