@@ -170,6 +170,87 @@ ppl_status ppl_infer_is_instance(const ppl_model* model, const ppl_data* data,
                                  ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,
                                  ppl_stream stream);
 
+/* One shard's share of a likelihood-weighting pass whose particles are split
+ * over several GPUs (or calls) by contiguous ranges of the global particle
+ * index: the particle-based inference the paper names as future work (§6)
+ * scales out because its normalisation (§3.6.2) is a reduction over all
+ * samples, and per-degree partials merge like the blocks of one kernel.
+ * Opaque, 384 bytes; [dev] buffers of it must be 16-byte aligned. */
+typedef struct {
+  unsigned char opaque[384];
+} ppl_is_partial;
+
+/* Likelihood weighting on particles [first_particle, first_particle +
+ * n_particles) of a population: trace i of this call draws as particle
+ * first_particle + i of ppl_infer_is_instance (same seed and instance), so a
+ * population split over shards draws exactly the traces of the unsplit call.
+ * Writes this shard's partial to *partial_dev [dev]; lw_out and
+ * particles_out [dev, n_particles] (optional) are indexed by i, and a
+ * record's origin is its global particle index.  Data sets of at most 2048
+ * points (the tensor-core trace kernel); first_particle + n_particles <
+ * 2^31.  Workspace: ppl_workspace_size(model, n_particles, data->len). */
+ppl_status ppl_infer_is_partial(const ppl_model* model, const ppl_data* data,
+                                int64_t first_particle, int64_t n_particles, uint64_t seed,
+                                uint32_t instance, ppl_is_partial* partial_dev, float* lw_out,
+                                ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,
+                                ppl_stream stream);
+
+/* The summary of a population from its shards' partials, partials_dev [dev,
+ * n_partials] (e.g. gathered from every rank), into *out_dev [dev].  The
+ * result is that of ppl_infer_is_instance on the whole population up to the
+ * order of FP32/FP64 roundings in the merge (maxima, argmax and counts are
+ * exact).  A shard's device error is reported in out_dev->status; no finite
+ * weight anywhere -> PPL_EEMPTY. */
+ppl_status ppl_is_merge(const ppl_is_partial* partials_dev, int32_t n_partials,
+                        ppl_is_result* out_dev, ppl_stream stream);
+
+/* Sharded systematic resampling (particle methods across devices, §6): a
+ * population of n_total particles split by contiguous ranges of the global
+ * index, m outputs.  The fixed-point weights are those of ppl_resample on the
+ * whole population (its maximum log-weight, the scale 2^(61 - ceil(log2
+ * n_total))), so the ancestors are those of the unsplit call bit for bit:
+ *  1. each shard: ppl_logsumexp gives its maximum; the maximum over shards
+ *     (an all-reduce) is the population's;
+ *  2. each shard: ppl_resample_shard_total -> its sum of fixed-point weights;
+ *  3. every shard, from all shards' sums in shard order (an all-gather):
+ *     ppl_resample_shard_plan -> each shard's plan;
+ *  4. each shard: ppl_resample_shard -> the ancestors (global indices) of its
+ *     outputs [k_first, k_end), which all descend from its own particles,
+ *     and optionally their gathered records. */
+typedef struct {
+  uint64_t total, stride, offset; /* the population's T, floor(T / m), u */
+  uint64_t c_base;                /* sum of the fixed-point weights of the shards before */
+  int64_t k_first, k_end;         /* this shard's outputs */
+  int64_t m, n_total;
+} ppl_resample_plan;
+
+/* The sum of the shard's fixed-point weights into *total_dev [dev, u64]:
+ * lw [dev, n_local], *max_lw_dev [dev, FP64] the population's maximum.  A
+ * log-weight above it sets PPL_EINVAL in the workspace status.  Workspace:
+ * ppl_workspace_size(any model, 1, 0). */
+ppl_status ppl_resample_shard_total(const float* lw, int64_t n_local, const double* max_lw_dev,
+                                    int64_t n_total, uint64_t* total_dev, void* ws,
+                                    size_t ws_bytes, ppl_stream stream);
+
+/* Host only (no device work): the plans of n_shards shards from their sums
+ * totals [host, n_shards], in shard order, into plans [host, n_shards].  The
+ * offset u is the resampling draw of ppl_resample (step t, instance).
+ * Every weight zero -> PPL_EEMPTY; sums above 2^61 or below m -> PPL_EINVAL. */
+ppl_status ppl_resample_shard_plan(const uint64_t* totals, int32_t n_shards, int64_t n_total,
+                                   int64_t m, uint64_t seed, uint32_t instance, uint32_t t,
+                                   ppl_resample_plan* plans);
+
+/* One shard's resampling: ancestors [dev, k_end - k_first] gets, for output
+ * k of the population, the global index of its ancestor at ancestors[k -
+ * k_first].  With state_in [dev, n_local records of stride_bytes, a multiple
+ * of 4 up to 1024, 4-byte aligned] the records of those outputs' ancestors
+ * are copied to state_out [dev, k_end - k_first records].  `plan` [host] is
+ * this shard's entry.  Workspace: ppl_workspace_size(any model, n_local, 0). */
+ppl_status ppl_resample_shard(const float* lw, int64_t n_local, int64_t first_particle,
+                              const double* max_lw_dev, const ppl_resample_plan* plan,
+                              int32_t* ancestors, const void* state_in, int64_t stride_bytes,
+                              void* state_out, void* ws, size_t ws_bytes, ppl_stream stream);
+
 /* ppl_infer_is_instance with the factor evaluated from the data's
  * sufficient statistics instead of point by point.  The model of Fig. 1 is
  * linear in its coefficients, so with Phi the matrix of powers x_l^j,

@@ -61,6 +61,7 @@ class PplIsResult(ctypes.Structure):
 
 
 RESULT_BYTES = ctypes.sizeof(PplIsResult)
+PARTIAL_BYTES = 384  # ppl_is_partial
 
 class PplCustomdistModel(ctypes.Structure):
     _fields_ = [("w1", ctypes.c_float), ("mu1", ctypes.c_float), ("sigma1", ctypes.c_float),
@@ -99,6 +100,13 @@ class PplDiscreteResult(ctypes.Structure):
                 "n_particles": self.n_particles, "n_values": n, "status": self.status,
                 "value": np.array(self.value[:n]), "prob": np.array(self.prob[:n]),
                 "count": np.array(self.count[:n])}
+
+
+class PplResamplePlan(ctypes.Structure):
+    _fields_ = [("total", ctypes.c_uint64), ("stride", ctypes.c_uint64),
+                ("offset", ctypes.c_uint64), ("c_base", ctypes.c_uint64),
+                ("k_first", ctypes.c_int64), ("k_end", ctypes.c_int64),
+                ("m", ctypes.c_int64), ("n_total", ctypes.c_int64)]
 
 
 class PplBatchPlan(ctypes.Structure):
@@ -218,6 +226,22 @@ _SIGS = {
     "ppl_posterior_reduce": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_size_t, ctypes.c_void_p]),
+    "ppl_infer_is_partial": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64,
+                                            ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
+                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                            ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "ppl_is_merge": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                    ctypes.c_void_p]),
+    "ppl_resample_shard_total": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                                ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_size_t, ctypes.c_void_p]),
+    "ppl_resample_shard_plan": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64,
+                                               ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
+                                               ctypes.c_uint32, ctypes.c_void_p]),
+    "ppl_resample_shard": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64,
+                                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
 }
 
 
@@ -568,6 +592,89 @@ def ppl_posterior_reduce(model, particles, lw=None, out=None, ws=None, stream=No
                                     _ptr(out), _ptr(ws), ws.numel(), _stream(stream))
     _check(st, "ppl_posterior_reduce")
     return out
+
+
+def partial_tensor(n_partials=1, device="cuda"):
+    """Device storage for n_partials ppl_is_partial records (16-byte aligned)."""
+    return torch.zeros((n_partials, PARTIAL_BYTES), dtype=torch.uint8, device=device)
+
+
+def ppl_infer_is_partial(model, x, y, first_particle, n_particles, seed, instance=0,
+                         partial=None, lw_out=None, particles_out=None, ws=None, stream=None):
+    """One shard's partial of likelihood weighting over particles
+    [first_particle, first_particle + n_particles); returns the partial buffer."""
+    _dev_f32(x, "x")
+    _dev_f32(y, "y")
+    if ws is None:
+        ws = workspace(model, n_particles, x.numel(), x.device)
+    if partial is None:
+        partial = partial_tensor(1, x.device)
+    data = PplData(x.data_ptr(), y.data_ptr(), x.numel())
+    st = lib().ppl_infer_is_partial(ctypes.byref(model), ctypes.byref(data), int(first_particle),
+                                    int(n_particles), ctypes.c_uint64(seed), int(instance),
+                                    _ptr(partial), _ptr(lw_out), _ptr(particles_out), _ptr(ws),
+                                    ws.numel(), _stream(stream))
+    _check(st, "ppl_infer_is_partial")
+    return partial
+
+
+def ppl_is_merge(partials, out=None, stream=None):
+    """The population's summary from its shards' partials [P, PARTIAL_BYTES] (device)."""
+    if partials.dim() != 2 or partials.shape[1] != PARTIAL_BYTES or not partials.is_contiguous():
+        raise ValueError("partials must be a contiguous [P, 384] uint8 device tensor")
+    if out is None:
+        out = result_tensor(partials.device)
+    st = lib().ppl_is_merge(_ptr(partials), partials.shape[0], _ptr(out), _stream(stream))
+    _check(st, "ppl_is_merge")
+    return out
+
+
+def ppl_resample_shard_total(lw, max_lw_dev, n_total, total=None, ws=None, stream=None):
+    """This shard's sum of fixed-point weights (a uint64 device scalar, as int64 storage)."""
+    _dev_f32(lw, "lw")
+    if ws is None:
+        ws = workspace(poly_model(), 1, 0, lw.device)
+    if total is None:
+        total = torch.zeros(1, dtype=torch.int64, device=lw.device)
+    st = lib().ppl_resample_shard_total(_ptr(lw), lw.numel(), _ptr(max_lw_dev), int(n_total),
+                                        _ptr(total), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "ppl_resample_shard_total")
+    return total
+
+
+def ppl_resample_shard_plan(totals, n_total, m, seed, instance=0, t=0):
+    """Host: every shard's plan from the shards' sums (uint64, shard order)."""
+    tot = np.ascontiguousarray(np.asarray(totals, dtype=np.uint64))
+    plans = (PplResamplePlan * len(tot))()
+    st = lib().ppl_resample_shard_plan(tot.ctypes.data_as(ctypes.c_void_p), len(tot), int(n_total),
+                                       int(m), ctypes.c_uint64(seed), int(instance), int(t), plans)
+    _check(st, "ppl_resample_shard_plan")
+    return list(plans)
+
+
+def ppl_resample_shard(lw, first_particle, max_lw_dev, plan, ancestors=None, state_in=None,
+                       state_out=None, ws=None, stream=None):
+    """This shard's outputs [plan.k_first, plan.k_end): (ancestors, state_out)."""
+    _dev_f32(lw, "lw")
+    n_out = plan.k_end - plan.k_first
+    if ws is None:
+        ws = workspace(poly_model(), lw.numel(), 0, lw.device)
+    if ancestors is None:
+        ancestors = torch.empty(max(n_out, 1), dtype=torch.int32, device=lw.device)
+    stride = 0
+    if state_in is not None:
+        if not state_in.is_contiguous():
+            raise ValueError("state_in must be contiguous")
+        stride = state_in[0].numel() * state_in.element_size() if state_in.dim() > 1 else \
+            state_in.element_size()
+        if state_out is None:
+            state_out = torch.empty((max(n_out, 1),) + tuple(state_in.shape[1:]),
+                                    dtype=state_in.dtype, device=state_in.device)
+    st = lib().ppl_resample_shard(_ptr(lw), lw.numel(), int(first_particle), _ptr(max_lw_dev),
+                                  ctypes.byref(plan), _ptr(ancestors), _ptr(state_in), stride,
+                                  _ptr(state_out), _ptr(ws), ws.numel(), _stream(stream))
+    _check(st, "ppl_resample_shard")
+    return ancestors[:n_out], (state_out[:n_out] if state_out is not None else None)
 
 
 def poly_particles(n, device="cuda"):

@@ -87,6 +87,29 @@ ppl_status poly_params(const ppl_model* m, PolyParams* p) {
   return PPL_OK;
 }
 
+// Word 0 of Philox4x32-10 (Salmon, Moraes, Dror and Shaw, SC'11) on the
+// host, with the counter layout of the device draws: key = (seed lo, seed
+// hi), counter = (particle, instance, step, purpose << 16 | block).
+uint32_t host_philox_word0(uint64_t seed, uint32_t particle, uint32_t instance, uint32_t step,
+                           uint32_t purpose, uint32_t block) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = particle, c1 = instance, c2 = step, c3 = (purpose << 16) | block;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    const uint64_t p0 = (uint64_t)M0 * c0, p1 = (uint64_t)M1 * c2;
+    const uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0, n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+    c1 = (uint32_t)p1;
+    c3 = (uint32_t)p0;
+    c0 = n0;
+    c2 = n2;
+  }
+  return c0;
+}
+
 #define PPL_TRY(expr)                      \
   do {                                     \
     const ppl_status _st = (expr);         \
@@ -456,6 +479,127 @@ ppl_status ppl_posterior_reduce(const ppl_model* model, const ppl_poly_particle*
   PPL_TRY(reset_ws(w, false, s));
   PPL_TRY(cuda_status(cudaMemsetAsync(out_dev, 0, sizeof(ppl_is_result), s)));
   PPL_TRY(cuda_status(launch_posterior(p, particles, lw, n, w.hdr(), w.partials(), out_dev, s)));
+  return PPL_OK;
+}
+
+ppl_status ppl_infer_is_partial(const ppl_model* model, const ppl_data* data,
+                                int64_t first_particle, int64_t n_particles, uint64_t seed,
+                                uint32_t instance, ppl_is_partial* partial_dev, float* lw_out,
+                                ppl_poly_particle* particles_out, void* ws, size_t ws_bytes,
+                                ppl_stream stream) {
+  PolyParams p;
+  PPL_TRY(poly_params(model, &p));
+  if (!data || data->len < 0 || (data->len > 0 && (!data->x || !data->y))) return PPL_EINVAL;
+  if (data->len > trace_tc_max_points()) return PPL_EINVAL;
+  if (first_particle < 0 || n_particles < 1 || first_particle + n_particles > kMaxParticles ||
+      !partial_dev || (reinterpret_cast<uintptr_t>(partial_dev) & 15))
+    return PPL_EINVAL;
+  if (particles_out && (reinterpret_cast<uintptr_t>(particles_out) & 15)) return PPL_EINVAL;
+  Ws w;
+  PPL_TRY(check_ws(ws, ws_bytes, n_particles, data->len, &w));
+  cudaStream_t s = (cudaStream_t)stream;
+  PPL_TRY(reset_ws(w, false, s));
+  PPL_TRY(cuda_status(launch_poly_trace_tc(p, data->x, data->y, data->len, n_particles, seed,
+                                           instance, lw_out, particles_out, w.hdr(),
+                                           w.partials(), nullptr, s, first_particle,
+                                           partial_dev)));
+  return PPL_OK;
+}
+
+ppl_status ppl_is_merge(const ppl_is_partial* partials_dev, int32_t n_partials,
+                        ppl_is_result* out_dev, ppl_stream stream) {
+  if (!partials_dev || !out_dev || n_partials < 1 || n_partials > 65536 ||
+      (reinterpret_cast<uintptr_t>(partials_dev) & 15))
+    return PPL_EINVAL;
+  return cuda_status(launch_merge_shards(partials_dev, n_partials, out_dev,
+                                         (cudaStream_t)stream));
+}
+
+ppl_status ppl_resample_shard_total(const float* lw, int64_t n_local, const double* max_lw_dev,
+                                    int64_t n_total, uint64_t* total_dev, void* ws,
+                                    size_t ws_bytes, ppl_stream stream) {
+  if (!lw || !max_lw_dev || !total_dev || n_local < 1 || n_total < n_local ||
+      n_total > kMaxParticles)
+    return PPL_EINVAL;
+  Ws w;
+  PPL_TRY(check_ws(ws, ws_bytes, 1, 0, &w));
+  cudaStream_t s = (cudaStream_t)stream;
+  PPL_TRY(reset_ws(w, false, s));
+  PPL_TRY(cuda_status(cudaMemsetAsync(total_dev, 0, sizeof(uint64_t), s)));
+  return cuda_status(launch_shard_total(lw, n_local, n_total, max_lw_dev, total_dev, w.hdr(), s));
+}
+
+ppl_status ppl_resample_shard_plan(const uint64_t* totals, int32_t n_shards, int64_t n_total,
+                                   int64_t m, uint64_t seed, uint32_t instance, uint32_t t,
+                                   ppl_resample_plan* plans) {
+  if (!totals || !plans || n_shards < 1 || m < 1 || m > kMaxParticles || n_total < 1 ||
+      n_total > kMaxParticles)
+    return PPL_EINVAL;
+  // T = sum of the shards' totals (each at most 2^61: the quantisation
+  // bounds the whole population's sum by 2^61)
+  uint64_t T = 0;
+  for (int32_t g = 0; g < n_shards; ++g) {
+    if (totals[g] > (1ull << 61) || T + totals[g] > (1ull << 61)) return PPL_EINVAL;
+    T += totals[g];
+  }
+  if (T == 0) return PPL_EEMPTY;
+  if (T < (uint64_t)m) return PPL_EINVAL;
+  const uint64_t stride = T / (uint64_t)m;
+  const uint32_t w = host_philox_word0(seed, 0, instance, t, 3 /* resampling offset */, 0);
+  const uint64_t u = (uint64_t)(((unsigned __int128)w * stride) >> 32);
+  // K(c) = #{k < m : u + k stride < c}
+  auto K = [&](uint64_t c) -> int64_t {
+    if (c <= u) return 0;
+    const uint64_t k = (c - u + stride - 1) / stride;
+    return k < (uint64_t)m ? (int64_t)k : m;
+  };
+  uint64_t c = 0;
+  for (int32_t g = 0; g < n_shards; ++g) {
+    ppl_resample_plan& p = plans[g];
+    p.total = T;
+    p.stride = stride;
+    p.offset = u;
+    p.c_base = c;
+    p.k_first = K(c);
+    c += totals[g];
+    p.k_end = K(c);
+    p.m = m;
+    p.n_total = n_total;
+  }
+  return PPL_OK;
+}
+
+ppl_status ppl_resample_shard(const float* lw, int64_t n_local, int64_t first_particle,
+                              const double* max_lw_dev, const ppl_resample_plan* plan,
+                              int32_t* ancestors, const void* state_in, int64_t stride_bytes,
+                              void* state_out, void* ws, size_t ws_bytes, ppl_stream stream) {
+  if (!lw || !max_lw_dev || !plan || n_local < 1 || first_particle < 0 ||
+      first_particle + n_local > plan->n_total || plan->n_total > kMaxParticles ||
+      plan->k_first < 0 || plan->k_end < plan->k_first || plan->k_end > plan->m ||
+      plan->stride == 0)
+    return PPL_EINVAL;
+  if (plan->k_end > plan->k_first && !ancestors) return PPL_EINVAL;
+  if (state_in || state_out) {
+    if (!state_in || !state_out || stride_bytes <= 0 || stride_bytes > 1024 || stride_bytes % 4 ||
+        ((reinterpret_cast<uintptr_t>(state_in) | reinterpret_cast<uintptr_t>(state_out)) & 3))
+      return PPL_EINVAL;
+  }
+  Ws w;
+  PPL_TRY(check_ws(ws, ws_bytes, n_local, 0, &w));
+  cudaStream_t s = (cudaStream_t)stream;
+  PPL_TRY(reset_ws(w, true, s));
+  ResampleShard sh;
+  sh.n_total = plan->n_total;
+  sh.first_particle = first_particle;
+  sh.k_first = plan->k_first;
+  sh.k_end = plan->k_end;
+  sh.stride = plan->stride;
+  sh.offset = plan->offset;
+  sh.c_base = plan->c_base;
+  PPL_TRY(cuda_status(launch_resample_coop(
+      lw, nullptr, max_lw_dev, n_local, plan->m, 0, 0, 0, w.hdr(), w.tiles(),
+      reinterpret_cast<char*>(w.prefix()), w.l.bounds - w.l.prefix, ancestors, nullptr, s,
+      state_in, state_in ? stride_bytes : 0, state_out, &sh)));
   return PPL_OK;
 }
 

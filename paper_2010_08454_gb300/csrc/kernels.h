@@ -26,11 +26,16 @@ cudaError_t launch_poly_trace(const PolyParams& p, const float* x, const float* 
                               ppl_is_result* res, cudaStream_t s, const void* suff = nullptr);
 // trace_tc.cu: the same pass with the factor's polynomial evaluations on the
 // tensor cores (data sets of up to trace_tc_max_points() points).
+// With part_out, the shard partial of particles [first, first + N) of a
+// larger population instead of the summary (trace i is particle first + i).
 int trace_tc_max_points();
 cudaError_t launch_poly_trace_tc(const PolyParams& p, const float* x, const float* y, int64_t L,
                                  int64_t N, uint64_t seed, uint32_t instance, float* lw_out,
                                  ppl_poly_particle* rec_out, WsHeader* hdr, void* parts,
-                                 ppl_is_result* res, cudaStream_t s);
+                                 ppl_is_result* res, cudaStream_t s, int64_t first = 0,
+                                 void* part_out = nullptr);
+// The summary of a population from P shard partials.
+cudaError_t launch_merge_shards(const void* parts, int P, ppl_is_result* res, cudaStream_t s);
 // Sufficient statistics of a data set for the line-fitting factor (one
 // block); `out` holds suffstat_bytes() bytes, 16-byte aligned.
 size_t suffstat_bytes();
@@ -97,6 +102,15 @@ size_t smc_run_workspace(int64_t N, int64_t T);
 // the grid barrier's words (resample_coop_barrier_bytes(), 128-byte aligned,
 // zeroed by the caller before the launch); `scratch` the per-chunk tables
 // (resample_coop_scratch(n) bytes, 16-byte aligned).
+// With `shard`, one shard of a population split over devices: n is the
+// shard's particle count, m the population's output count; the weights are
+// quantised for n_total particles with the population's maximum (known_max),
+// the layout is the shard plan's, and the call writes the shard's outputs
+// [k_first, k_end): anc[k - k_first] = first_particle + local ancestor.
+struct ResampleShard {
+  int64_t n_total, first_particle, k_first, k_end;
+  uint64_t stride, offset, c_base;
+};
 size_t resample_coop_scratch(int64_t n);
 size_t resample_coop_barrier_bytes();
 cudaError_t launch_resample_coop(const float* lw, const uint64_t* q_fixed, const double* known_max,
@@ -104,7 +118,12 @@ cudaError_t launch_resample_coop(const float* lw, const uint64_t* q_fixed, const
                                  WsHeader* hdr, void* barrier, char* scratch, size_t scratch_bytes,
                                  int32_t* anc, const int32_t* gate, cudaStream_t s,
                                  const void* rec_in = nullptr, int64_t rec_bytes = 0,
-                                 void* rec_out = nullptr);
+                                 void* rec_out = nullptr, const ResampleShard* shard = nullptr);
+// The sum of a shard's fixed-point weights (quantised for n_total particles
+// against *known_max) added to *total (zeroed by the caller).
+cudaError_t launch_shard_total(const float* lw, int64_t n, int64_t n_total,
+                               const double* known_max, uint64_t* total, WsHeader* hdr,
+                               cudaStream_t s);
 cudaError_t launch_smc_persistent(const LgssmParams& p, const float* y, int32_t T, uint64_t seed,
                                   int64_t N, float* x_out, float* lw_out, double* logz,
                                   int32_t* resampled, double* ess, char* ws, size_t ws_bytes,

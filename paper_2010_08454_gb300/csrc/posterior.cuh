@@ -337,4 +337,118 @@ __device__ __forceinline__ void finalize_partials(const DegPartial* parts, int G
 }
 
 
+
+// ---------------------------------------------------------------------------
+// One shard's share of a likelihood-weighting pass whose particles are split
+// over several devices: its per-degree partials merged (FP32 means and
+// second moments, FP64 sums around each degree's maximum), its particle
+// count and device status.  Shards merge exactly like blocks (§3.6.2: the
+// normalisation runs over all samples, wherever they were drawn).
+// ---------------------------------------------------------------------------
+struct __align__(16) IsPartial {
+  DegPartial deg[kMaxDegrees];
+  double S[kMaxDegrees], S2[kMaxDegrees];
+  int64_t n;
+  int32_t status, n_deg, min_deg, pad0;
+  unsigned char pad[32];
+};
+static_assert(sizeof(IsPartial) == 384, "the public ppl_is_partial is 384 bytes");
+
+// The last block's merge of the block partials into a shard partial (the
+// first part of finalize_partials, without the summary).
+__device__ __forceinline__ void finalize_to_partial(const DegPartial* parts, int G, int n_deg,
+                                                    int min_deg, int64_t N, WsHeader* hdr,
+                                                    IsPartial* out) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp < kMaxDegrees) {
+    DegPartial a;
+    deg_empty(a);
+    for (int b = lane; b < G; b += 32) deg_merge(a, parts[b * kMaxDegrees + warp]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const DegPartial other = deg_shfl_xor(a, o);
+      deg_merge(a, other);
+    }
+    const float M = a.m;
+    double s = 0.0, s2 = 0.0;
+    if (M != -INFINITY) {
+      for (int b = lane; b < G; b += 32) {
+        const DegPartial& q = parts[b * kMaxDegrees + warp];
+        if (q.m == -INFINITY) continue;
+        const double e = (double)expf(q.m - M);
+        s += (double)q.S * e;
+        s2 += (double)q.S2 * e * e;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+      out->deg[warp] = a;
+      out->S[warp] = s;
+      out->S2[warp] = s2;
+    }
+  }
+  if (threadIdx.x == 0) {
+    out->n = N;
+    out->n_deg = n_deg;
+    out->min_deg = min_deg;
+    out->status = ld_volatile_i32(&hdr->status);
+  }
+}
+
+// Merge of P shard partials into the summary of the whole population, by one
+// block: warp k merges degree k (the maxima exactly, means and second
+// moments by the parallel rule in FP32, the sums rescaled to the merged
+// maximum in FP64).  N is the total particle count.
+__device__ __forceinline__ void merge_shard_partials(const IsPartial* parts, int P, int64_t N,
+                                                     int32_t status, ppl_is_result* res) {
+  __shared__ DegPartial fin[kMaxDegrees];
+  __shared__ double fS[kMaxDegrees], fS2[kMaxDegrees];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n_deg = parts[0].n_deg, min_deg = parts[0].min_deg;
+  if (warp < kMaxDegrees) {
+    DegPartial a;
+    deg_empty(a);
+    for (int g = lane; g < P; g += 32) deg_merge(a, parts[g].deg[warp]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const DegPartial other = deg_shfl_xor(a, o);
+      deg_merge(a, other);
+    }
+    const float M = a.m;
+    double s = 0.0, s2 = 0.0;
+    if (M != -INFINITY) {
+      for (int g = lane; g < P; g += 32) {
+        const float m = parts[g].deg[warp].m;
+        if (m == -INFINITY) continue;
+        const double e = (double)expf(m - M);
+        s += parts[g].S[warp] * e;
+        s2 += parts[g].S2[warp] * e * e;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) {
+      fin[warp] = a;
+      fS[warp] = s;
+      fS2[warp] = s2;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int32_t st = status;
+    for (int g = 0; g < P && st == 0; ++g) st = parts[g].status;
+    bool any = false;
+    for (int k = 0; k < n_deg; ++k) any |= fin[k].m != -INFINITY;
+    if (st == 0 && !any) st = PPL_EEMPTY;
+    write_summary(fin, fS, fS2, n_deg, min_deg, N, st, res);
+  }
+}
+
 }  // namespace ppl

@@ -20,6 +20,12 @@
 //      merge path", ICS 2012), one equal slice of the merge per lane; an item
 //      whose outputs all have one ancestor is filled directly.  With a record
 //      buffer the warp then copies its outputs' records (the fused gather).
+//      A chunk that lies wholly inside one block's run and has at most two
+//      outputs per particle (near-uniform weights) is written instead in the
+//      scatter form of the same definition: particle j's offspring are the
+//      outputs [K(C_{j-1}), K(C_j)), K(c) = #{k : u + k stride < c}; the
+//      block writes the chunk's ancestors into a table in shared memory,
+//      then the ancestors and the records output by output.
 //
 // Every item costs at most 4096 weights and 256 outputs whatever the weights
 // are: a chunk holding most of the mass (degenerate importance weights)
@@ -47,6 +53,8 @@ constexpr int kRcBatch = 32;                          // chunks summed between b
 // items over the blocks, so that a block whose run crosses many sparsely
 // used chunks takes correspondingly fewer items.
 constexpr int kRcPrefixCost = 128;
+constexpr int kRcShort = 4;      // offspring a lane writes alone in the scatter form
+constexpr int kRcScatterOut = 2 * (int)kRcChunk;  // outputs of a chunk written in the scatter form
 constexpr int kRcJobBlk = 8;     // chunk totals the layout job's first pass loads at once per thread
 constexpr int kRcJobPer = 4;     // chunks per thread in a tile of the layout job
 constexpr int kRcJobTile = kRcTpb * kRcJobPer;
@@ -73,6 +81,15 @@ struct RcArgs {
   void* rec_out;
   int32_t rec_words;
   int32_t rec_word4;
+  // one shard of a population split over devices (planned != 0): the
+  // weights are quantised for a population of n_scale particles, the layout
+  // (stride, u) and this shard's exclusive prefix c_base are given, its
+  // outputs are [k_off, k_end) of m, ancestors[k - k_off] = j_off + local
+  // ancestor, rec_out[k - k_off]
+  int64_t n_scale;
+  int32_t planned;
+  uint64_t p_stride, p_u, c_base;
+  int64_t k_off, k_end, j_off;
 };
 
 // The records of outputs k0 .. k0 + nB - 1 of an item, by one warp: output j
@@ -105,6 +122,44 @@ __device__ __forceinline__ void gather_item(const RcArgs& a, int64_t k0, int nB,
   else
     gather_words(reinterpret_cast<const uint4*>(a.rec_in), reinterpret_cast<uint4*>(a.rec_out),
                  a.rec_words, k0, nB, anc_of, lane);
+}
+
+// The records of outputs k0 .. k0 + n - 1 by the whole block, from the
+// ancestors in shared memory: thread t copies words t, t + kRcTpb, .., four
+// loads in flight before their stores (coalesced on both sides, the
+// ancestors being non-decreasing).
+template <typename V>
+__device__ __forceinline__ void gather_block_words(const V* __restrict__ in, V* __restrict__ out,
+                                                   int W, int64_t k0, int n, const int32_t* sOut,
+                                                   int tid) {
+  const int total = n * W;
+  out += k0 * W;
+  for (int e0 = tid; e0 < total; e0 += 4 * kRcTpb) {
+    V v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = e0 + q * kRcTpb;
+      if (e < total) {
+        const int j = e / W;
+        v[q] = in[(int64_t)sOut[j] * W + (e - j * W)];
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = e0 + q * kRcTpb;
+      if (e < total) out[e] = v[q];
+    }
+  }
+}
+
+__device__ __forceinline__ void gather_block(const RcArgs& a, int64_t k0, int n,
+                                             const int32_t* sOut, int tid) {
+  if (a.rec_word4)
+    gather_block_words(reinterpret_cast<const uint32_t*>(a.rec_in),
+                       reinterpret_cast<uint32_t*>(a.rec_out), a.rec_words, k0, n, sOut, tid);
+  else
+    gather_block_words(reinterpret_cast<const uint4*>(a.rec_in), reinterpret_cast<uint4*>(a.rec_out),
+                       a.rec_words, k0, n, sOut, tid);
 }
 
 // The weights of one thread's kRcItems particles from `base`: FP32
@@ -268,6 +323,7 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
   uint64_t* sA = reinterpret_cast<uint64_t*>(rc_dyn);  // [kRcChunk] prefix sums of a chunk
   uint64_t* sL2 = sA + kRcChunk;                        // [kRcTpb] every 8th of them
   int32_t* sW = reinterpret_cast<int32_t*>(sL2 + kRcTpb);  // [warp][kRcItemOut] ancestors
+  int32_t* sOut = sW + kRcWarps * kRcItemOut;  // [kRcScatterOut] a scattered chunk's ancestors
   __shared__ uint64_t sL1[kRcChunk / 256];  // every 256th prefix sum
   static_assert(3 * kRcJobTile * 8 <= kRcChunk * 8 + kRcTpb * 8 + kRcWarps * kRcItemOut * 4,
                 "the layout job's tile tables fit in the dynamic shared memory");
@@ -282,7 +338,7 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
   if (FROM_LW) {
     m_lw = a.known_max ? (float)*a.known_max : a.hdr->max_lw;
     int S = 0;
-    while (((int64_t)1 << S) < a.n) ++S;
+    while (((int64_t)1 << S) < a.n_scale) ++S;
     scale = __int_as_float((127 + 61 - S) << 23);  // 2^(61 - ceil(log2 n))
   }
 
@@ -347,12 +403,19 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
     if (lane == 0) jtot[warp] = run;
     __syncthreads();
     const uint64_t T = warp_sum_acc<false>(lane < kRcWarps ? jtot[lane] : 0ull);
-    const bool valid = T > 0 && T <= (1ull << 61) && T >= (uint64_t)a.m;
+    bool valid;
     uint64_t stride = 0, u = 0;
-    if (valid) {
-      stride = T / (uint64_t)a.m;
-      const uint64_t w = philox_block(a.seed, 0, a.instance, a.t, kResample, 0).x;
-      u = (__umul64hi(w, stride) << 32) | ((w * stride) >> 32);
+    if (a.planned) {  // a shard: the population's layout is given
+      valid = T <= (1ull << 61) && a.p_stride > 0;
+      stride = a.p_stride;
+      u = a.p_u;
+    } else {
+      valid = T > 0 && T <= (1ull << 61) && T >= (uint64_t)a.m;
+      if (valid) {
+        stride = T / (uint64_t)a.m;
+        const uint64_t w = philox_block(a.seed, 0, a.instance, a.t, kResample, 0).x;
+        u = (__umul64hi(w, stride) << 32) | ((w * stride) >> 32);
+      }
     }
     const DivInv sv = div_inv(stride);
     // a chunk with outputs costs its items plus kRcPrefixCost
@@ -367,7 +430,7 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
     uint64_t* jC = reinterpret_cast<uint64_t*>(rc_dyn);
     int64_t* jK = reinterpret_cast<int64_t*>(rc_dyn + kRcJobTile * 8);
     int64_t* jI = reinterpret_cast<int64_t*>(rc_dyn + 2 * kRcJobTile * 8);
-    uint64_t carry_c = 0;
+    uint64_t carry_c = a.planned ? a.c_base : 0ull;  // prefixes in the population's terms
     int64_t carry_i = 0;
     for (int64_t t0 = 0; t0 < a.n_chunks; t0 += kRcJobTile) {
       const int nt = (int)(a.n_chunks - t0 < kRcJobTile ? a.n_chunks - t0 : kRcJobTile);
@@ -426,12 +489,12 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
     }
     const int64_t n_items = carry_i;
     if (tid == 0) {
-      if (T == 0) record_status(&a.hdr->status, PPL_EEMPTY);
-      else if (T > (1ull << 61) || T < (uint64_t)a.m) record_status(&a.hdr->status, PPL_EINVAL);
+      if (!a.planned && T == 0) record_status(&a.hdr->status, PPL_EEMPTY);
+      else if (!valid) record_status(&a.hdr->status, PPL_EINVAL);
       a.g->total = T;
       a.g->stride = stride;
       a.g->offset = u;
-      a.kfirst[a.n_chunks] = a.m;
+      a.kfirst[a.n_chunks] = a.planned ? a.k_end : a.m;
       a.ioff[a.n_chunks] = n_items;
     }
     return valid ? (unsigned long long)n_items : 0ull;
@@ -443,6 +506,7 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
   if (!ok) return;
   const int64_t n_items = (int64_t)(rel & ((1ull << 34) - 1));
   const uint64_t stride = view[1], u = view[2];
+  const DivInv sv = div_inv(stride);
 
   // 3. work items: block b takes the contiguous run [I b / G, I (b + 1) / G)
   // of cost units and walks it chunk by chunk.  Chunk c's units are
@@ -461,6 +525,10 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
     const bool more = io1 < it1;  // another chunk follows in this block's run
     const int64_t cb = ch * kRcChunk;
     const int64_t xs = it > io0 + kRcPrefixCost ? it : io0 + kRcPrefixCost;  // first item unit
+    // a chunk wholly inside this block's run, with at most two outputs per
+    // particle on average, is written in the scatter form (below)
+    const int nCw = (int)(a.n - cb < kRcChunk ? a.n - cb : kRcChunk);
+    const bool scatter = it <= io0 && seg_sh[cur][2] <= it1 && kn - kc <= kRcScatterOut;
     if (xs < io1) {  // the same for every thread of the block: the chunk's inclusive
       // prefix sums, every 8th and every 256th
       uint64_t p[kRcItems];
@@ -485,7 +553,41 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
     // warp 0 fetches the next chunk's descriptor while the others take this
     // chunk's items
     if (more && warp == 0) seg_lookup(a, io1, ch + 1, seg_sh[cur ^ 1], lane);
-    if (xs < io1 && !(more && warp == 0)) {
+    if (xs < io1 && scatter) {
+      // the scatter form of the same definition: particle j's offspring are
+      // the outputs k with C_{j-1} <= u + k stride < C_j, i.e. [K(C_{j-1}),
+      // K(C_j)) with K(c) = positions below c.  Lane l of a warp takes
+      // particle 32 w + l of each 512-particle slice and writes its
+      // ancestor index into the chunk's output table in shared memory (a
+      // particle with more than kRcShort offspring by its whole warp); the
+      // block then writes the ancestors and gathers the records output by
+      // output, several loads in flight per thread.
+      const int n_out = (int)(kn - kc);
+      for (int j0 = 0; j0 < nCw; j0 += kRcTpb) {
+        const int j = j0 + tid;  // the same slice for the whole warp
+        const bool has = j < nCw;
+        const int64_t ke = has ? positions_below_inv(sA[j], u, sv, a.m) : a.m;
+        int64_t ks = __shfl_up_sync(0xffffffffu, ke, 1);
+        if (lane == 0)
+          ks = has ? positions_below_inv(j == 0 ? cstart : sA[j - 1], u, sv, a.m) : a.m;
+        const int32_t an = (int32_t)(cb + j);
+        const bool longr = has && ke - ks > kRcShort;
+        if (has && !longr)
+          for (int64_t k = ks; k < ke; ++k) sOut[k - kc] = an;
+        unsigned lm = __ballot_sync(0xffffffffu, longr);
+        while (lm) {
+          const int src = __ffs(lm) - 1;
+          lm &= lm - 1;
+          const int s0 = (int)(__shfl_sync(0xffffffffu, ks, src) - kc);
+          const int s1 = (int)(__shfl_sync(0xffffffffu, ke, src) - kc);
+          const int32_t as = __shfl_sync(0xffffffffu, an, src);
+          for (int k = s0 + lane; k < s1; k += 32) sOut[k] = as;
+        }
+      }
+      __syncthreads();
+      for (int e = tid; e < n_out; e += kRcTpb) a.anc[kc - a.k_off + e] = sOut[e] + (int32_t)a.j_off;
+      if (a.rec_words > 0) gather_block(a, kc - a.k_off, n_out, sOut, tid);
+    } else if (xs < io1 && !(more && warp == 0)) {
       const int nC = (int)(a.n - cb < kRcChunk ? a.n - cb : kRcChunk);
       const int w0 = more ? 1 : 0, nw = kRcWarps - w0;
       for (int64_t x = xs + (warp - w0); x < io1; x += nw) {
@@ -498,8 +600,9 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
         const int ia = chunk_first_above(sA, sL2, sL1, pos0, lane);
         if (posl < sA[ia]) {  // one ancestor for the whole item (degenerate weights)
           const int32_t an = (int32_t)(cb + ia);
-          for (int jj = lane; jj < nB; jj += 32) a.anc[k0 + jj] = an;
-          if (a.rec_words > 0) gather_item(a, k0, nB, [an](int) { return an; }, lane);
+          for (int jj = lane; jj < nB; jj += 32) a.anc[k0 - a.k_off + jj] = an + (int32_t)a.j_off;
+          if (a.rec_words > 0)
+            gather_item(a, k0 - a.k_off, nB, [an](int) { return an; }, lane);
           continue;
         }
         const int ib = min(chunk_first_above(sA, sL2, sL1, posl, lane) + 1, nC);
@@ -527,14 +630,57 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
           }
         }
         __syncwarp();
-        for (int jj = lane; jj < nB; jj += 32) a.anc[k0 + jj] = sWw[jj];
-        if (a.rec_words > 0) gather_item(a, k0, nB, [sWw](int j) { return sWw[j]; }, lane);
+        for (int jj = lane; jj < nB; jj += 32) a.anc[k0 - a.k_off + jj] = sWw[jj] + (int32_t)a.j_off;
+        if (a.rec_words > 0)
+          gather_item(a, k0 - a.k_off, nB, [sWw](int j) { return sWw[j]; }, lane);
         __syncwarp();  // sWw is rewritten by the warp's next item
       }
     }
     __syncthreads();  // sA, its index and seg_sh are rewritten for the next chunk
     it = io1;
   }
+}
+
+// The sum of one shard's fixed-point weights, quantised exactly as the whole
+// population's (its maximum, the scale of n_total particles): block sums of
+// u64 integers added atomically (integer addition, so the order does not
+// matter).  A weight above the given maximum is an error.
+__global__ void __launch_bounds__(kTpb) shard_total_kernel(const float* __restrict__ lw, int64_t n,
+                                                           int64_t n_total,
+                                                           const double* known_max,
+                                                           uint64_t* total, WsHeader* hdr) {
+  __shared__ uint64_t wsum[kTpb / 32];
+  const float m = (float)*known_max;
+  int S = 0;
+  while (((int64_t)1 << S) < n_total) ++S;
+  const float scale = __int_as_float((127 + 61 - S) << 23);
+  uint64_t t = 0;
+  int bad = 0;
+  for (int64_t i = (int64_t)blockIdx.x * kTpb + threadIdx.x; i < n; i += (int64_t)gridDim.x * kTpb) {
+    const float v = lw[i];
+    bad |= v > m;
+    t += v > m ? 0ull : quantize(v, m, scale);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) wsum[warp] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t b = 0;
+    for (int w = 0; w < kTpb / 32; ++w) b += wsum[w];
+    atomicAdd(reinterpret_cast<unsigned long long*>(total), (unsigned long long)b);
+  }
+  if (bad) record_status(&hdr->status, PPL_EINVAL);
+}
+
+cudaError_t launch_shard_total(const float* lw, int64_t n, int64_t n_total,
+                               const double* known_max, uint64_t* total, WsHeader* hdr,
+                               cudaStream_t s) {
+  const int grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>((n + kTpb - 1) / kTpb, (int64_t)num_sms() * 8));
+  shard_total_kernel<<<grid, kTpb, 0, s>>>(lw, n, n_total, known_max, total, hdr);
+  return cudaGetLastError();
 }
 
 size_t resample_coop_scratch(int64_t n) {
@@ -548,7 +694,8 @@ cudaError_t launch_resample_coop(const float* lw, const uint64_t* q_fixed, const
                                  int64_t n, int64_t m, uint64_t seed, uint32_t instance, uint32_t t,
                                  WsHeader* hdr, void* barrier, char* scratch, size_t scratch_bytes,
                                  int32_t* anc, const int32_t* gate, cudaStream_t s,
-                                 const void* rec_in, int64_t rec_bytes, void* rec_out) {
+                                 const void* rec_in, int64_t rec_bytes, void* rec_out,
+                                 const ResampleShard* shard) {
   if (scratch_bytes < resample_coop_scratch(n) || (reinterpret_cast<uintptr_t>(scratch) & 15) ||
       (reinterpret_cast<uintptr_t>(barrier) & 127))
     return cudaErrorInvalidValue;
@@ -565,6 +712,14 @@ cudaError_t launch_resample_coop(const float* lw, const uint64_t* q_fixed, const
   a.anc = anc;
   a.gate = gate;
   a.n_chunks = (n + kRcChunk - 1) / kRcChunk;
+  a.n_scale = shard ? shard->n_total : n;
+  a.planned = shard ? 1 : 0;
+  a.p_stride = shard ? shard->stride : 0;
+  a.p_u = shard ? shard->offset : 0;
+  a.c_base = shard ? shard->c_base : 0;
+  a.k_off = shard ? shard->k_first : 0;
+  a.k_end = shard ? shard->k_end : m;
+  a.j_off = shard ? shard->first_particle : 0;
   a.rec_in = rec_in;
   a.rec_out = rec_out;
   a.rec_words = 0;
@@ -588,7 +743,8 @@ cudaError_t launch_resample_coop(const float* lw, const uint64_t* q_fixed, const
   a.kfirst = reinterpret_cast<int64_t*>(take((size_t)(a.n_chunks + 1) * 8));
   a.ioff = reinterpret_cast<int64_t*>(take((size_t)(a.n_chunks + 1) * 8));
   constexpr size_t dyn = (size_t)kRcChunk * sizeof(uint64_t) + (size_t)kRcTpb * sizeof(uint64_t) +
-                         (size_t)kRcWarps * kRcItemOut * sizeof(int32_t);
+                         (size_t)kRcWarps * kRcItemOut * sizeof(int32_t) +
+                         (size_t)kRcScatterOut * sizeof(int32_t);
   const void* fn = lw ? (const void*)resample_coop_kernel<true> : (const void*)resample_coop_kernel<false>;
   static int per_sm_of[2] = {0, 0};  // set up once per kernel: attribute and residency
   int& per_sm = per_sm_of[lw ? 1 : 0];

@@ -330,9 +330,9 @@ __device__ __forceinline__ void fold_warp(DegPartial* wr, float lw, int d, int i
 
 __global__ void __launch_bounds__(kTcThreads, 1) poly_trace_tc_kernel(
     PolyParams p, const float* __restrict__ xs, const float* __restrict__ ys, int L, int Lp,
-    int64_t N, uint64_t seed, uint32_t instance, float* __restrict__ lw_out,
+    int64_t N, int64_t first, uint64_t seed, uint32_t instance, float* __restrict__ lw_out,
     ppl_poly_particle* __restrict__ rec_out, WsHeader* hdr, DegPartial* parts,
-    ppl_is_result* res) {
+    ppl_is_result* res, IsPartial* part_out) {
   extern __shared__ __align__(1024) unsigned char tc_dyn[];
   // A operands: [warpgroup][hi, lo] x 4 KB; then B hi and lo, Lp x 32 B each
   unsigned char* a_base = tc_dyn;
@@ -411,17 +411,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) poly_trace_tc_kernel(
   int64_t tile = kTcWGs * (int64_t)blockIdx.x + g;
   float c[kMaxCoef];
   int n = 0;
+  // trace i of this call is particle first + i of the population: its draws
+  // and its recorded origin use the particle index
   auto draw_tile = [&](int64_t t, float (&cc)[kMaxCoef], int& nn) {
     const int64_t i = t * kTcM + r;
+    const uint32_t gi = (uint32_t)(first + (i < N ? i : 0));
     float corr;
-    nn = draw((uint32_t)(i < N ? i : 0), cc, corr);
+    nn = draw(gi, cc, corr);
     if (i < N && rec_out) {
       if (rec_v8) {
-        st_record_v8(rec_out + i, cc, nn, (uint32_t)i);
+        st_record_v8(rec_out + i, cc, nn, gi);
       } else {
         float4* dst = reinterpret_cast<float4*>(rec_out + i);
         dst[0] = make_float4(cc[0], cc[1], cc[2], cc[3]);
-        dst[1] = make_float4(cc[4], cc[5], __int_as_float(nn), __uint_as_float((uint32_t)i));
+        dst[1] = make_float4(cc[4], cc[5], __int_as_float(nn), __uint_as_float(gi));
       }
     }
   };
@@ -492,7 +495,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) poly_trace_tc_kernel(
     if (stop) break;
     const float lw = ss * p.neg_half_inv_var;
     if (valid && lw_out) lw_out[i] = lw;
-    fold_warp(wr, lw, valid ? n - p.min_deg : -1, (int)i, c, lane, nan);
+    fold_warp(wr, lw, valid ? n - p.min_deg : -1, (int)(first + i), c, lane, nan);
     if (next < n_tiles) {
 #pragma unroll
       for (int k = 0; k < kMaxCoef; ++k) c[k] = cn[k];
@@ -527,8 +530,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) poly_trace_tc_kernel(
     if (lane == 0) parts[blockIdx.x * kMaxDegrees + warp] = q;
   }
   if (tid == 0 && sh.nan) record_status(&hdr->status, PPL_ENAN);
-  if (elect_last_block(&hdr->ticket[0]))
-    finalize_partials(parts, gridDim.x, p.n_deg, p.min_deg, N, hdr, res);
+  if (elect_last_block(&hdr->ticket[0])) {
+    if (part_out) finalize_to_partial(parts, gridDim.x, p.n_deg, p.min_deg, N, hdr, part_out);
+    else finalize_partials(parts, gridDim.x, p.n_deg, p.min_deg, N, hdr, res);
+  }
+}
+
+// The summary of a population from its shards' partials (one block); the
+// population's size is the sum of the shards'.
+__global__ void __launch_bounds__(256) merge_shards_kernel(const IsPartial* parts, int P,
+                                                           ppl_is_result* res) {
+  __shared__ int64_t n_sh;
+  if (threadIdx.x == 0) {
+    int64_t n = 0;
+    for (int g = 0; g < P; ++g) n += parts[g].n;
+    n_sh = n;
+  }
+  __syncthreads();
+  merge_shard_partials(parts, P, n_sh, 0, res);
 }
 
 constexpr int kTcMaxDevices = 64;
@@ -543,10 +562,16 @@ size_t trace_tc_smem(int64_t L) {
   return (size_t)kTcWGs * 8192 + (size_t)Lp * 64;
 }
 
+cudaError_t launch_merge_shards(const void* parts, int P, ppl_is_result* res, cudaStream_t s) {
+  merge_shards_kernel<<<1, 256, 0, s>>>((const IsPartial*)parts, P, res);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_poly_trace_tc(const PolyParams& p, const float* x, const float* y, int64_t L,
                                  int64_t N, uint64_t seed, uint32_t instance, float* lw_out,
                                  ppl_poly_particle* rec_out, WsHeader* hdr, void* parts,
-                                 ppl_is_result* res, cudaStream_t s) {
+                                 ppl_is_result* res, cudaStream_t s, int64_t first,
+                                 void* part_out) {
   if (L < 0 || L > kTcMaxPoints) return cudaErrorInvalidValue;
   const int Lp = (int)((L + 31) / 32 * 32);
   const size_t smem = trace_tc_smem(L);
@@ -568,9 +593,10 @@ cudaError_t launch_poly_trace_tc(const PolyParams& p, const float* x, const floa
   const int64_t tiles = (N + kTcM - 1) / kTcM;
   const int grid = (int)std::max<int64_t>(
       1, std::min<int64_t>((tiles + kTcWGs - 1) / kTcWGs, num_sms()));
-  poly_trace_tc_kernel<<<grid, kTcThreads, smem, s>>>(p, x, y, (int)L, Lp, N, seed, instance,
-                                                      lw_out, rec_out, hdr,
-                                                      (DegPartial*)parts, res);
+  poly_trace_tc_kernel<<<grid, kTcThreads, smem, s>>>(p, x, y, (int)L, Lp, N, first, seed,
+                                                      instance, lw_out, rec_out, hdr,
+                                                      (DegPartial*)parts, res,
+                                                      (IsPartial*)part_out);
   return cudaGetLastError();
 }
 
