@@ -210,13 +210,12 @@ static cudaError_t launch_batched_t(const PolyParams& p, const float* x, const f
   e = cudaMemsetAsync(ws + l.inst_max, 0, (size_t)n_inst * kMaxDegrees * sizeof(int32_t), s);
   if (e != cudaSuccess) return e;
   const size_t smem = trace_smem_bytes<PPT>() + kBatchChunk * sizeof(float2);
-  static bool attr_set = false;
-  if (!attr_set) {
-    e = cudaFuncSetAttribute(batched_kernel<PPT, LEARNED>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  int unused = 0;
+  e = device_once((const void*)batched_kernel<PPT, LEARNED>, &unused, [smem](int*) {
+    return cudaFuncSetAttribute(batched_kernel<PPT, LEARNED>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  });
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<PPT, LEARNED>, kTpb,
                                                     smem);

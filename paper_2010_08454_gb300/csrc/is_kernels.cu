@@ -3,6 +3,9 @@
 // posterior reduction fused in (degree masses, weighted coefficient means and
 // variances, the mode), the statistics pass over given log-weights, and the
 // one-pass posterior summary of a given population.
+#include <map>
+#include <mutex>
+
 #include "kernels.h"
 #include "poly.cuh"
 #include "posterior.cuh"
@@ -449,16 +452,36 @@ __global__ void __launch_bounds__(kTpb) posterior_kernel(PolyParams p,
 // ---------------------------------------------------------------------------
 // Host launchers.
 // ---------------------------------------------------------------------------
-static int g_num_sms = 0;
+namespace {
+std::mutex g_once_mutex;
+std::map<std::pair<const void*, int>, int> g_once_value;
+}  // namespace
+
+cudaError_t device_once(const void* key, int* value, const std::function<cudaError_t(int*)>& setup) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(g_once_mutex);
+  auto it = g_once_value.find({key, dev});
+  if (it == g_once_value.end()) {
+    int v = 0;
+    e = setup(&v);
+    if (e != cudaSuccess) return e;
+    it = g_once_value.emplace(std::make_pair(key, dev), v).first;
+  }
+  *value = it->second;
+  return cudaSuccess;
+}
 
 int num_sms() {
-  if (!g_num_sms) {
+  int n = 0;
+  const cudaError_t e = device_once((const void*)&num_sms, &n, [](int* v) {
     int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_num_sms <= 0) g_num_sms = 1;
-  }
-  return g_num_sms;
+    cudaError_t r = cudaGetDevice(&dev);
+    if (r == cudaSuccess) r = cudaDeviceGetAttribute(v, cudaDevAttrMultiProcessorCount, dev);
+    return r;
+  });
+  return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
 constexpr int kTraceKernelPpt = 4;
@@ -483,17 +506,14 @@ cudaError_t launch_poly_trace(const PolyParams& p, const float* x, const float* 
   constexpr int PPT = kTraceKernelPpt;
   const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(L, kMaxChunk));
   const size_t smem = trace_smem_bytes<PPT>() + (size_t)chunk * sizeof(float2);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(poly_trace_kernel<PPT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(trace_smem_bytes<PPT>() + kMaxChunk * sizeof(float2)));
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  int unused = 0;
+  cudaError_t e = device_once((const void*)poly_trace_kernel<PPT>, &unused, [](int*) {
+    return cudaFuncSetAttribute(poly_trace_kernel<PPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(trace_smem_bytes<PPT>() + kMaxChunk * sizeof(float2)));
+  });
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, poly_trace_kernel<PPT>,
-                                                                kTpb, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, poly_trace_kernel<PPT>, kTpb, smem);
   if (e != cudaSuccess) return e;
   const int grid = std::max(1, std::min(trace_grid(N), num_sms() * std::max(1, per_sm)));
   poly_trace_kernel<PPT><<<grid, kTpb, smem, s>>>(p, x, y, L, N, seed, instance, chunk, lw_out,

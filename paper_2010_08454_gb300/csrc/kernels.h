@@ -7,12 +7,20 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <functional>
 
 #include "common.cuh"
 
 namespace ppl {
 
 struct PolyParams;
+
+// Host set-up that must run once per device (a kernel's shared-memory
+// attribute, a residency count): runs `setup` the first time `key` is seen
+// with the current device, under a lock, and returns the int it produced
+// then and on every later call for that (key, device).  A failed set-up is
+// not cached.
+cudaError_t device_once(const void* key, int* value, const std::function<cudaError_t(int*)>& setup);
 
 int num_sms();
 int trace_grid(int64_t N);

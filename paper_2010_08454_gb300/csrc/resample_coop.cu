@@ -746,16 +746,16 @@ cudaError_t launch_resample_coop(const float* lw, const uint64_t* q_fixed, const
                          (size_t)kRcWarps * kRcItemOut * sizeof(int32_t) +
                          (size_t)kRcScatterOut * sizeof(int32_t);
   const void* fn = lw ? (const void*)resample_coop_kernel<true> : (const void*)resample_coop_kernel<false>;
-  static int per_sm_of[2] = {0, 0};  // set up once per kernel: attribute and residency
-  int& per_sm = per_sm_of[lw ? 1 : 0];
-  if (per_sm == 0) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
-    if (e != cudaSuccess) return e;
-    int r = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&r, fn, kRcTpb, dyn);
-    if (e != cudaSuccess) return e;
-    per_sm = r > 0 ? r : 1;
-  }
+  // once per kernel and device: the shared-memory attribute and the residency
+  int per_sm = 0;
+  const cudaError_t e = device_once(fn, &per_sm, [fn](int* v) {
+    cudaError_t r = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (r != cudaSuccess) return r;
+    r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(v, fn, kRcTpb, dyn);
+    if (r == cudaSuccess && *v < 1) *v = 1;
+    return r;
+  });
+  if (e != cudaSuccess) return e;
   const int64_t grid = (int64_t)num_sms() * per_sm;
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel(fn, dim3((unsigned)grid), dim3(kRcTpb), args, dyn, s);

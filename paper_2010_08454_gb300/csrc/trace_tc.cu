@@ -39,8 +39,6 @@
 // skipped), and the last CTA merges the CTAs' partials.
 // Every mbarrier wait is bounded; a wait that runs out records PPL_ETIMEOUT,
 // and the CTA still frees its tensor memory.
-#include <mutex>
-
 #include "kernels.h"
 #include "poly.cuh"
 #include "posterior.cuh"
@@ -550,10 +548,6 @@ __global__ void __launch_bounds__(256) merge_shards_kernel(const IsPartial* part
   merge_shard_partials(parts, P, n_sh, 0, res);
 }
 
-constexpr int kTcMaxDevices = 64;
-std::mutex g_tc_mutex;
-bool g_tc_attr[kTcMaxDevices] = {false};
-
 // Largest data set the tensor-core trace kernel stages in shared memory.
 int trace_tc_max_points() { return kTcMaxPoints; }
 
@@ -577,19 +571,12 @@ cudaError_t launch_poly_trace_tc(const PolyParams& p, const float* x, const floa
   const size_t smem = trace_tc_smem(L);
   // the largest shared-memory size, once per device (the attribute is per
   // device; setting it is a slow host call)
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  int unused = 0;
+  cudaError_t e = device_once((const void*)poly_trace_tc_kernel, &unused, [](int*) {
+    return cudaFuncSetAttribute(poly_trace_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)trace_tc_smem(kTcMaxPoints));
+  });
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kTcMaxDevices) return cudaErrorInvalidDevice;
-  {
-    std::lock_guard<std::mutex> lock(g_tc_mutex);
-    if (!g_tc_attr[dev]) {
-      e = cudaFuncSetAttribute(poly_trace_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)trace_tc_smem(kTcMaxPoints));
-      if (e != cudaSuccess) return e;
-      g_tc_attr[dev] = true;
-    }
-  }
   const int64_t tiles = (N + kTcM - 1) / kTcM;
   const int grid = (int)std::max<int64_t>(
       1, std::min<int64_t>((tiles + kTcWGs - 1) / kTcWGs, num_sms()));

@@ -207,13 +207,12 @@ cudaError_t launch_umma_gemm(const __nv_bfloat16* A, int64_t sam, int64_t sak,
                              const __nv_bfloat16* B, int64_t sbn, int64_t sbk, int M, int N, int K,
                              const float* bias, const __nv_bfloat16* mask, int relu, float* Cf,
                              __nv_bfloat16* Cb, int32_t* status, cudaStream_t s) {
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e = cudaFuncSetAttribute(
-        umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUmmaSmem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  int unused = 0;
+  const cudaError_t e = device_once((const void*)umma_gemm_kernel, &unused, [](int*) {
+    return cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kUmmaSmem);
+  });
+  if (e != cudaSuccess) return e;
   UmmaArgs g;
   g.A = A; g.sam = sam; g.sak = sak;
   g.B = B; g.sbn = sbn; g.sbk = sbk;
