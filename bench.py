@@ -523,11 +523,35 @@ def bench_learned(torch, ppl, epochs=4, n_sets=1024, N=1 << 20, reps=3):
     params = ppl.pack_params(synth.mlp_weights(1))
     am, av = torch.zeros_like(params), torch.zeros_like(params)
     n_pairs, batch = 1 << 20, 1024
+    steps = epochs * (n_pairs // batch)
+    block = 64  # training steps per CUDA graph replay
+    pws = ppl.proposal_workspace(batch)
+    # first-call set-up outside the capture, on scratch copies
+    sp, sm, sv = params.clone(), am.clone(), av.clone()
+    ppl.ppl_proposal_train_init(sp, batch, pws)
+    ppl.ppl_proposal_train_steps(model, sp, sm, sv, n_pairs, batch, 1, 99, 1e-3, None, pws)
+    ppl.ppl_proposal_train_init(params, batch, pws)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        ppl.ppl_proposal_train_steps(model, params, am, av, n_pairs, batch, block, 99, 1e-3,
+                                     None, pws)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    ppl.ppl_proposal_train(model, params, am, av, n_pairs, batch, epochs, 99, 1e-3)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(steps // block):
+        graph.replay()
+    ev1.record()
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
+    train_ms = ev0.elapsed_time(ev1)
+    if ppl.ppl_workspace_status(pws) != 0:
+        raise RuntimeError("training: device status")
+    # FLOPs of a step: forward 64x256 + 256x256 + 256x48 multiply-adds per
+    # pair, and twice that backward (weight and input gradients)
+    step_flops = 3 * 2 * (64 * 256 + 256 * 256 + 256 * 48) * batch
+    bf16 = (load_peaks() or {}).get("bf16_tflops")
     d = synth.prior_datasets(n_sets, 32, 4)
     x, y = torch.from_numpy(d["x"]).cuda(), torch.from_numpy(d["y"]).cuda()
     xf, yf = x.reshape(-1).contiguous(), y.reshape(-1).contiguous()
@@ -571,7 +595,14 @@ def bench_learned(torch, ppl, epochs=4, n_sets=1024, N=1 << 20, reps=3):
                       "ess_per_sec_at_tol": float(ess_p[ok_p].sum() / (ms_p / 1e3)),
                       "frac_within_0.05": float(ok_p.mean()), "median_abs_err": float(np.median(ep)),
                       "median_ess": float(np.median(ess_p)), "ms": ms_p},
-            "train_seconds": train_s, "train_steps": epochs * (n_pairs // batch)}
+            "train_seconds": train_s, "train_steps": steps,
+            "train": {"ms_per_step": train_ms / steps, "graph_block_steps": block,
+                      "tflops": step_flops * steps / (train_ms / 1e3) / 1e12,
+                      "bf16_peak_tflops": bf16,
+                      "frac": (step_flops * steps / (train_ms / 1e3) / 1e12 / bf16) if bf16 else None,
+                      "work": "3 x 2 x (64 x 256 + 256 x 256 + 256 x 48) FLOP per pair, "
+                              "1024 pairs per step",
+                      "timing": "CUDA events around the graph replays of all steps"}}
 
 
 def run_reference(args):

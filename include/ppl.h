@@ -479,6 +479,17 @@ ppl_status ppl_batched_status(const void* ws, ppl_stream stream);
  *  ppl_proposal_train: Adam (lr, 0.9, 0.999, 1e-8) on params with moments
  *    adam_m, adam_v [dev, FP32, zero-initialised], epochs x (n_pairs / batch)
  *    steps over pairs 0 .. n_pairs - 1; loss_per_step [dev, FP64] optional.
+ *    It is ppl_proposal_train_init followed by ppl_proposal_train_steps of
+ *    every step.
+ *  ppl_proposal_train_init: zeroes the training run's step counter in `ws`
+ *    and converts params to the BF16 copy the products read.
+ *  ppl_proposal_train_steps: n_steps more steps of the run that `ws` holds.
+ *    Step s (the counter, kept on the device) trains on pairs (s mod
+ *    (n_pairs / batch)) batch .. + batch - 1 and writes its summed loss to
+ *    loss_per_step[s]; nothing a step does depends on host values, so the
+ *    enqueued work of one call (about 17 launches per step) can be captured
+ *    once in a CUDA graph by the caller and replayed for every later block of
+ *    steps.
  *  ppl_infer_is_learned: ppl_infer_is_batched with each instance's draws from
  *    its proposal (proposal [dev, FP32, n_inst x 48], e.g. from
  *    ppl_proposal_forward); a proposal equal to the prior gives the prior run. */
@@ -496,6 +507,13 @@ ppl_status ppl_proposal_train(const ppl_model* model, float* params, float* adam
                               float* adam_v, int64_t n_pairs, int32_t batch, int32_t epochs,
                               uint64_t seed, float lr, double* loss_per_step, void* ws,
                               size_t ws_bytes, ppl_stream stream);
+ppl_status ppl_proposal_train_init(const float* params, int32_t batch, void* ws,
+                                   size_t ws_bytes, ppl_stream stream);
+ppl_status ppl_proposal_train_steps(const ppl_model* model, float* params, float* adam_m,
+                                    float* adam_v, int64_t n_pairs, int32_t batch,
+                                    int32_t n_steps, uint64_t seed, float lr,
+                                    double* loss_per_step, void* ws, size_t ws_bytes,
+                                    ppl_stream stream);
 ppl_status ppl_infer_is_learned(const ppl_model* model, const float* x, const float* y,
                                 const int64_t* data_off, const int64_t* part_off,
                                 int32_t n_inst, uint64_t seed, const ppl_batch_plan* plan,

@@ -218,6 +218,13 @@ _SIGS = {
                                           ctypes.c_int32, ctypes.c_uint64, ctypes.c_float,
                                           ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                           ctypes.c_void_p]),
+    "ppl_proposal_train_init": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                               ctypes.c_size_t, ctypes.c_void_p]),
+    "ppl_proposal_train_steps": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_uint64, ctypes.c_float,
+                                                ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                                ctypes.c_void_p]),
     "ppl_infer_is_learned": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                             ctypes.c_uint64, ctypes.c_void_p, ctypes.c_void_p,
@@ -812,6 +819,20 @@ def ppl_proposal_train(model, params, adam_m, adam_v, n_pairs, batch, epochs, se
                                     _ptr(adam_v), int(n_pairs), int(batch), int(epochs),
                                     ctypes.c_uint64(seed), float(lr), _ptr(loss_per_step),
                                     _ptr(ws), ws.numel(), _stream(stream)), "ppl_proposal_train")
+
+
+def ppl_proposal_train_init(params, batch, ws, stream=None):
+    _check(lib().ppl_proposal_train_init(_ptr(params), int(batch), _ptr(ws), ws.numel(),
+                                         _stream(stream)), "ppl_proposal_train_init")
+
+
+def ppl_proposal_train_steps(model, params, adam_m, adam_v, n_pairs, batch, n_steps, seed,
+                             lr=1e-3, loss_per_step=None, ws=None, stream=None):
+    _check(lib().ppl_proposal_train_steps(ctypes.byref(model), _ptr(params), _ptr(adam_m),
+                                          _ptr(adam_v), int(n_pairs), int(batch), int(n_steps),
+                                          ctypes.c_uint64(seed), float(lr), _ptr(loss_per_step),
+                                          _ptr(ws), ws.numel(), _stream(stream)),
+           "ppl_proposal_train_steps")
 
 
 def ppl_infer_is_learned(model, x, y, data_off, part_off, seed, plan, proposal, out, ws,

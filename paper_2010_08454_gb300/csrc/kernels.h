@@ -47,10 +47,14 @@ cudaError_t launch_merge_shards(const void* parts, int P, ppl_is_result* res, cu
 // Sufficient statistics of a data set for the line-fitting factor (one
 // block); `out` holds suffstat_bytes() bytes, 16-byte aligned.
 size_t suffstat_bytes();
+// With split_ws (split_floats FP32 words of device scratch) the product may
+// be split along K over more CTAs, the slices summed in order by a second
+// kernel (the same result on every run).
 cudaError_t launch_umma_gemm(const __nv_bfloat16* A, int64_t sam, int64_t sak,
                              const __nv_bfloat16* B, int64_t sbn, int64_t sbk, int M, int N, int K,
                              const float* bias, const __nv_bfloat16* mask, int relu, float* Cf,
-                             __nv_bfloat16* Cb, int32_t* status, cudaStream_t s);
+                             __nv_bfloat16* Cb, int32_t* status, cudaStream_t s,
+                             float* split_ws = nullptr, size_t split_floats = 0);
 cudaError_t launch_customdist(const ppl_customdist_model& m, uint32_t comp_threshold,
                               const float* y, int64_t n, int64_t N, uint64_t seed, float* x_out,
                               float* lw_out, void* parts, WsHeader* hdr,

@@ -66,14 +66,20 @@ __global__ void __launch_bounds__(kTpb) features_kernel(const float* __restrict_
 // Training pair p (purpose FORWARD_SIM, instance 0): blocks 0, 1 draw the trace
 // as a prior trace; block 2 + l draws point l: x = 2 u01(w0) - 1 and
 // y = f(x) + obs_sigma BoxMuller(w1, w2).z0.
+// With `step` (a training run's device step counter, steps done so far) the
+// batch is pairs [(step mod steps_per_epoch) B, + B) instead of [pair0, + B),
+// so a run of training steps needs no value from the host.
 __global__ void __launch_bounds__(kTpb) forward_sim_kernel(PolyParams p, float obs_sigma,
                                                            uint64_t seed, int64_t pair0,
                                                            int32_t B,
                                                            __nv_bfloat16* __restrict__ feat,
                                                            int32_t* __restrict__ n_out,
-                                                           float* __restrict__ c_out) {
+                                                           float* __restrict__ c_out,
+                                                           const int32_t* step = nullptr,
+                                                           int64_t steps_per_epoch = 1) {
   const int warp = (blockIdx.x * kTpb + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (warp >= B) return;
+  if (step) pair0 = ((int64_t)*step % steps_per_epoch) * B;
   const uint32_t pair = (uint32_t)(pair0 + warp);
   const uint4 a = philox_block(seed, pair, 0, 0, kForwardSim, 0);
   const uint4 b = philox_block(seed, pair, 0, 0, kForwardSim, 1);
@@ -117,9 +123,13 @@ struct GemmArgs {
   __nv_bfloat16* Cb;   // BF16 output [M x N], optional
 };
 
-static cudaError_t gemm(const GemmArgs& g, int32_t* status, cudaStream_t s) {
+// Split-K scratch of the network's products: the largest product (256 x
+// 256) in up to 16 K slices.
+constexpr size_t kSplitFloats = (size_t)16 * 256 * 256;
+
+static cudaError_t gemm(const GemmArgs& g, int32_t* status, cudaStream_t s, float* split = nullptr) {
   return launch_umma_gemm(g.A, g.sam, g.sak, g.B, g.sbn, g.sbk, g.M, g.N, g.K, g.bias, g.mask,
-                          g.relu, g.Cf, g.Cb, status, s);
+                          g.relu, g.Cf, g.Cb, status, s, split, split ? kSplitFloats : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -227,7 +237,12 @@ __global__ void to_bf16_kernel(const float* __restrict__ p, __nv_bfloat16* __res
   if (i < n) pb[i] = __float2bfloat16_rn(p[i]);
 }
 
-__global__ void bump_kernel(int32_t* step) { *step += 1; }
+// The step counter advances; the step's summed loss goes to loss_out[step - 1].
+__global__ void bump_kernel(int32_t* step, const double* loss, double* loss_out) {
+  const int32_t s = *step + 1;
+  *step = s;
+  if (loss_out) loss_out[s - 1] = *loss;
+}
 
 // ---------------------------------------------------------------------------
 // Workspace of the network for a batch of B rows.
@@ -240,6 +255,7 @@ struct MlpWs {
   float* c_t;
   double* loss;
   int32_t* step;
+  float* split;  // split-K slices of the products
   size_t total;
 };
 
@@ -268,6 +284,7 @@ static MlpWs mlp_ws(char* base, int64_t B) {
   w.dh1 = (__nv_bfloat16*)take(B * kHid * 2);
   w.n_t = (int32_t*)take(B * 4);
   w.c_t = (float*)take(B * kMaxCoef * 4);
+  w.split = (float*)take(kSplitFloats * 4);
   w.total = off;
   return w;
 }
@@ -277,18 +294,18 @@ static cudaError_t mlp_forward(const float* params, const MlpWs& w, int B, cudaS
   g.A = w.feat; g.sam = kIn; g.sak = 1;
   g.B = w.pb + kOffW1; g.sbn = kIn; g.sbk = 1;
   g.M = B; g.N = kHid; g.K = kIn; g.bias = params + kOffB1; g.relu = 1; g.Cb = w.h1;
-  cudaError_t e = gemm(g, w.status, s);
+  cudaError_t e = gemm(g, w.status, s, w.split);
   if (e != cudaSuccess) return e;
   g = GemmArgs{};
   g.A = w.h1; g.sam = kHid; g.sak = 1;
   g.B = w.pb + kOffW2; g.sbn = kHid; g.sbk = 1;
   g.M = B; g.N = kHid; g.K = kHid; g.bias = params + kOffB2; g.relu = 1; g.Cb = w.h2;
-  if ((e = gemm(g, w.status, s)) != cudaSuccess) return e;
+  if ((e = gemm(g, w.status, s, w.split)) != cudaSuccess) return e;
   g = GemmArgs{};
   g.A = w.h2; g.sam = kHid; g.sak = 1;
   g.B = w.pb + kOffW3; g.sbn = kHid; g.sbk = 1;
   g.M = B; g.N = kOut; g.K = kHid; g.bias = params + kOffB3; g.Cf = w.out;
-  return gemm(g, w.status, s);
+  return gemm(g, w.status, s, w.split);
 }
 
 // Gradient of the mean loss over the batch into w.grad (FP32), loss sum into w.loss[0].
@@ -303,33 +320,33 @@ static cudaError_t mlp_backward(const ProposalShape& q, const MlpWs& w, int B, c
   g.A = w.dout_b; g.sam = 1; g.sak = kOut;
   g.B = w.h2; g.sbn = 1; g.sbk = kHid;
   g.M = kOut; g.N = kHid; g.K = B; g.Cf = w.grad + kOffW3;
-  if ((e = gemm(g, w.status, s)) != cudaSuccess) return e;
+  if ((e = gemm(g, w.status, s, w.split)) != cudaSuccess) return e;
   colsum_kernel<float><<<1, 64, 0, s>>>(w.dout, B, kOut, w.grad + kOffB3);
   // dh2[b, i] = sum_o dout[b, o] W3[o, i], masked by h2 > 0
   g = GemmArgs{};
   g.A = w.dout_b; g.sam = kOut; g.sak = 1;
   g.B = w.pb + kOffW3; g.sbn = 1; g.sbk = kHid;
   g.M = B; g.N = kHid; g.K = kOut; g.mask = w.h2; g.Cb = w.dh2;
-  if ((e = gemm(g, w.status, s)) != cudaSuccess) return e;
+  if ((e = gemm(g, w.status, s, w.split)) != cudaSuccess) return e;
   // dW2[o, i] = sum_b dh2[b, o] h1[b, i]
   g = GemmArgs{};
   g.A = w.dh2; g.sam = 1; g.sak = kHid;
   g.B = w.h1; g.sbn = 1; g.sbk = kHid;
   g.M = kHid; g.N = kHid; g.K = B; g.Cf = w.grad + kOffW2;
-  if ((e = gemm(g, w.status, s)) != cudaSuccess) return e;
+  if ((e = gemm(g, w.status, s, w.split)) != cudaSuccess) return e;
   colsum_kernel<__nv_bfloat16><<<1, kHid, 0, s>>>(w.dh2, B, kHid, w.grad + kOffB2);
   // dh1 = (dh2 W2) masked by h1 > 0
   g = GemmArgs{};
   g.A = w.dh2; g.sam = kHid; g.sak = 1;
   g.B = w.pb + kOffW2; g.sbn = 1; g.sbk = kHid;
   g.M = B; g.N = kHid; g.K = kHid; g.mask = w.h1; g.Cb = w.dh1;
-  if ((e = gemm(g, w.status, s)) != cudaSuccess) return e;
+  if ((e = gemm(g, w.status, s, w.split)) != cudaSuccess) return e;
   // dW1[o, i] = sum_b dh1[b, o] feat[b, i]
   g = GemmArgs{};
   g.A = w.dh1; g.sam = 1; g.sak = kHid;
   g.B = w.feat; g.sbn = 1; g.sbk = kIn;
   g.M = kHid; g.N = kIn; g.K = B; g.Cf = w.grad + kOffW1;
-  if ((e = gemm(g, w.status, s)) != cudaSuccess) return e;
+  if ((e = gemm(g, w.status, s, w.split)) != cudaSuccess) return e;
   colsum_kernel<__nv_bfloat16><<<1, kHid, 0, s>>>(w.dh1, B, kHid, w.grad + kOffB1);
   return cudaGetLastError();
 }
@@ -436,41 +453,59 @@ ppl_status ppl_proposal_grad(const ppl_model* model, const float* params, int64_
   return PPL_OK;
 }
 
-ppl_status ppl_proposal_train(const ppl_model* model, float* params, float* adam_m,
-                              float* adam_v, int64_t n_pairs, int32_t batch, int32_t epochs,
-                              uint64_t seed, float lr, double* loss_per_step, void* ws,
-                              size_t ws_bytes, ppl_stream stream) {
+ppl_status ppl_proposal_train_init(const float* params, int32_t batch, void* ws,
+                                   size_t ws_bytes, ppl_stream stream) {
+  if (!params || batch < 1 || !ws) return PPL_EINVAL;
+  MlpWs w = mlp_ws(static_cast<char*>(ws), batch);
+  if (ws_bytes < w.total) return PPL_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(w.status, 0, sizeof(int32_t), s) != cudaSuccess ||
+      cudaMemsetAsync(w.step, 0, sizeof(int32_t), s) != cudaSuccess)
+    return PPL_ECUDA;
+  to_bf16_kernel<<<(unsigned)((kNumParams + kTpb - 1) / kTpb), kTpb, 0, s>>>(params, w.pb,
+                                                                            kNumParams);
+  return st(cudaGetLastError());
+}
+
+ppl_status ppl_proposal_train_steps(const ppl_model* model, float* params, float* adam_m,
+                                    float* adam_v, int64_t n_pairs, int32_t batch,
+                                    int32_t n_steps, uint64_t seed, float lr,
+                                    double* loss_per_step, void* ws, size_t ws_bytes,
+                                    ppl_stream stream) {
   PolyParams p;
   if (mlp_model(model, &p) != PPL_OK || !params || !adam_m || !adam_v || batch < 1 ||
-      n_pairs < batch || epochs < 1 || !ws || !(lr > 0.0f) || n_pairs > 0xffffffffll)
+      n_pairs < batch || n_steps < 0 || !ws || !(lr > 0.0f) || n_pairs > 0xffffffffll)
     return PPL_EINVAL;
   MlpWs w = mlp_ws(static_cast<char*>(ws), batch);
   if (ws_bytes < w.total) return PPL_EINVAL;
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaMemsetAsync(w.status, 0, sizeof(int32_t), s) != cudaSuccess) return PPL_ECUDA;
   const ProposalShape q = shape_of(p, model->prior_sigma);
   const int64_t steps_per_epoch = n_pairs / batch;
-  if (cudaMemsetAsync(w.step, 0, sizeof(int32_t), s) != cudaSuccess) return PPL_ECUDA;
-  to_bf16_kernel<<<(unsigned)((kNumParams + kTpb - 1) / kTpb), kTpb, 0, s>>>(params, w.pb,
-                                                                            kNumParams);
-  for (int32_t ep = 0; ep < epochs; ++ep) {
-    for (int64_t it = 0; it < steps_per_epoch; ++it) {
-      forward_sim_kernel<<<(unsigned)(((int64_t)batch * 32 + kTpb - 1) / kTpb), kTpb, 0, s>>>(
-          p, model->obs_sigma, seed, it * batch, batch, w.feat, w.n_t, w.c_t);
-      ppl_status r = st(mlp_forward(params, w, batch, s));
-      if (r != PPL_OK) return r;
-      r = st(mlp_backward(q, w, batch, s));
-      if (r != PPL_OK) return r;
-      bump_kernel<<<1, 1, 0, s>>>(w.step);
-      adam_kernel<<<(unsigned)((kNumParams + kTpb - 1) / kTpb), kTpb, 0, s>>>(
-          params, w.grad, adam_m, adam_v, w.pb, kNumParams, lr, 0.9f, 0.999f, 1e-8f, w.step);
-      if (loss_per_step &&
-          cudaMemcpyAsync(loss_per_step + ep * steps_per_epoch + it, w.loss, sizeof(double),
-                          cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return PPL_ECUDA;
-    }
+  for (int32_t it = 0; it < n_steps; ++it) {
+    forward_sim_kernel<<<(unsigned)(((int64_t)batch * 32 + kTpb - 1) / kTpb), kTpb, 0, s>>>(
+        p, model->obs_sigma, seed, 0, batch, w.feat, w.n_t, w.c_t, w.step, steps_per_epoch);
+    ppl_status r = st(mlp_forward(params, w, batch, s));
+    if (r != PPL_OK) return r;
+    r = st(mlp_backward(q, w, batch, s));
+    if (r != PPL_OK) return r;
+    bump_kernel<<<1, 1, 0, s>>>(w.step, w.loss, loss_per_step);
+    adam_kernel<<<(unsigned)((kNumParams + kTpb - 1) / kTpb), kTpb, 0, s>>>(
+        params, w.grad, adam_m, adam_v, w.pb, kNumParams, lr, 0.9f, 0.999f, 1e-8f, w.step);
   }
   return st(cudaGetLastError());
+}
+
+ppl_status ppl_proposal_train(const ppl_model* model, float* params, float* adam_m,
+                              float* adam_v, int64_t n_pairs, int32_t batch, int32_t epochs,
+                              uint64_t seed, float lr, double* loss_per_step, void* ws,
+                              size_t ws_bytes, ppl_stream stream) {
+  if (epochs < 1 || batch < 1 || n_pairs < batch) return PPL_EINVAL;
+  const int64_t steps = (int64_t)epochs * (n_pairs / batch);
+  if (steps > 0x7fffffffll) return PPL_EINVAL;
+  ppl_status r = ppl_proposal_train_init(params, batch, ws, ws_bytes, stream);
+  if (r != PPL_OK) return r;
+  return ppl_proposal_train_steps(model, params, adam_m, adam_v, n_pairs, batch, (int32_t)steps,
+                                  seed, lr, loss_per_step, ws, ws_bytes, stream);
 }
 
 }  // extern "C"

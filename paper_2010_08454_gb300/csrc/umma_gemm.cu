@@ -37,6 +37,11 @@ struct UmmaArgs {
   __nv_bfloat16* Cb;  // BF16 output [M x N], optional
   int32_t* status;    // set to PPL_ETIMEOUT when a wait runs out
   int vec_a, vec_b;   // K contiguous, rows 16-byte aligned: 8 elements per load
+  // split-K: CTA z of grid.z takes K range [z k_split, (z + 1) k_split) and
+  // writes its raw FP32 tile to partial[z][M][N]; a second kernel sums the
+  // slices in order and applies the epilogue
+  float* partial;
+  int k_split;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -101,7 +106,9 @@ __global__ void __launch_bounds__(128) umma_gemm_kernel(UmmaArgs g) {
   const __nv_bfloat16 zero = __float2bfloat16_rn(0.0f);
   uint32_t phase = 0;
   bool any = false;
-  for (int k0 = 0; k0 < g.K; k0 += kUK) {
+  const int k_begin = g.partial ? (int)blockIdx.z * g.k_split : 0;
+  const int k_end = g.partial ? min(g.K, k_begin + g.k_split) : g.K;
+  for (int k0 = k_begin; k0 < k_end; k0 += kUK) {
     // stage the K tile (the previous tile's MMAs have completed)
     if (g.vec_a) {  // one core-matrix row (8 consecutive k) per 16-byte load
       for (int e = tid; e < kUM * (kUK / 8); e += 128) {
@@ -111,6 +118,13 @@ __global__ void __launch_bounds__(128) umma_gemm_kernel(UmmaArgs g) {
         if (gm < g.M && gk < g.K)  // K % 8 == 0: the whole row is in range
           v = *reinterpret_cast<const uint4*>(g.A + (int64_t)gm * g.sam + gk);
         *reinterpret_cast<uint4*>(As + core_index(r, k)) = v;
+      }
+    } else if (g.sam == 1) {  // rows contiguous: consecutive threads take consecutive rows
+      for (int e = tid; e < kUM * kUK; e += 128) {
+        const int r = e % kUM, k = e / kUM;
+        const int gm = m0 + r, gk = k0 + k;
+        As[core_index(r, k)] =
+            (gm < g.M && gk < g.K) ? g.A[gm + (int64_t)gk * g.sak] : zero;
       }
     } else {
       for (int e = tid; e < kUM * kUK; e += 128) {
@@ -128,6 +142,13 @@ __global__ void __launch_bounds__(128) umma_gemm_kernel(UmmaArgs g) {
           v = *reinterpret_cast<const uint4*>(g.B + (int64_t)gn * g.sbn + gk);
         *reinterpret_cast<uint4*>(Bs + core_index(r, k)) = v;
       }
+    } else if (g.sbn == 1) {  // columns contiguous: consecutive threads take consecutive columns
+      for (int e = tid; e < kUN * kUK; e += 128) {
+        const int r = e % kUN, k = e / kUN;
+        const int gn = n0 + r, gk = k0 + k;
+        Bs[core_index(r, k)] =
+            (gn < g.N && gk < g.K) ? g.B[gn + (int64_t)gk * g.sbk] : zero;
+      }
     } else {
       for (int e = tid; e < kUN * kUK; e += 128) {
         const int r = e / kUK, k = e % kUK;
@@ -143,7 +164,7 @@ __global__ void __launch_bounds__(128) umma_gemm_kernel(UmmaArgs g) {
       for (int kk = 0; kk < kUK / 16; ++kk) {
         const uint64_t ad = umma_desc(smem_u32(As) + kk * 2 * 128, 128, 1024);
         const uint64_t bd = umma_desc(smem_u32(Bs) + kk * 2 * 128, 128, 1024);
-        const uint32_t acc = (k0 > 0 || kk > 0) ? 1u : 0u;
+        const uint32_t acc = (k0 > k_begin || kk > 0) ? 1u : 0u;  // first step of the slice: overwrite
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
@@ -177,7 +198,14 @@ __global__ void __launch_bounds__(128) umma_gemm_kernel(UmmaArgs g) {
           : "r"(taddr)
           : "memory");
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (m < g.M) {
+      if (m < g.M && g.partial) {  // a K slice: the raw tile
+        float* dst = g.partial + ((int64_t)blockIdx.z * g.M + m) * g.N;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int n = n0 + c0 + j;
+          if (n < g.N) dst[n] = any ? __uint_as_float(v[j]) : 0.0f;
+        }
+      } else if (m < g.M) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
           const int n = n0 + c0 + j;
@@ -199,6 +227,21 @@ __global__ void __launch_bounds__(128) umma_gemm_kernel(UmmaArgs g) {
                  :: "r"(tmem), "r"(kUTmemCols) : "memory");
 }
 
+// The sum of the K slices in order (deterministic), then the epilogue.
+__global__ void __launch_bounds__(256) splitk_reduce_kernel(UmmaArgs g, int S) {
+  const int64_t e = (int64_t)blockIdx.x * 256 + threadIdx.x;
+  const int64_t MN = (int64_t)g.M * g.N;
+  if (e >= MN) return;
+  const int n = (int)(e % g.N);
+  float x = 0.0f;
+  for (int z = 0; z < S; ++z) x += g.partial[z * MN + e];
+  if (g.bias) x += g.bias[n];
+  if (g.relu) x = fmaxf(x, 0.0f);
+  if (g.mask && !(__bfloat162float(g.mask[e]) > 0.0f)) x = 0.0f;
+  if (g.Cf) g.Cf[e] = x;
+  if (g.Cb) g.Cb[e] = __float2bfloat16_rn(x);
+}
+
 // Shared memory per CTA (dynamic), sized so that at most four CTAs share an
 // SM: 4 x 64 tensor-memory columns stay within the SM's 512.
 constexpr size_t kUmmaSmem = 48 * 1024;
@@ -206,7 +249,8 @@ constexpr size_t kUmmaSmem = 48 * 1024;
 cudaError_t launch_umma_gemm(const __nv_bfloat16* A, int64_t sam, int64_t sak,
                              const __nv_bfloat16* B, int64_t sbn, int64_t sbk, int M, int N, int K,
                              const float* bias, const __nv_bfloat16* mask, int relu, float* Cf,
-                             __nv_bfloat16* Cb, int32_t* status, cudaStream_t s) {
+                             __nv_bfloat16* Cb, int32_t* status, cudaStream_t s,
+                             float* split_ws, size_t split_floats) {
   int unused = 0;
   const cudaError_t e = device_once((const void*)umma_gemm_kernel, &unused, [](int*) {
     return cudaFuncSetAttribute(umma_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -222,8 +266,26 @@ cudaError_t launch_umma_gemm(const __nv_bfloat16* A, int64_t sam, int64_t sak,
   // a 16-byte aligned base
   g.vec_a = sak == 1 && K % 8 == 0 && sam % 8 == 0 && (reinterpret_cast<uintptr_t>(A) & 15) == 0;
   g.vec_b = sbk == 1 && K % 8 == 0 && sbn % 8 == 0 && (reinterpret_cast<uintptr_t>(B) & 15) == 0;
+  g.partial = nullptr;
+  g.k_split = K;
   dim3 grid((N + kUN - 1) / kUN, (M + kUM - 1) / kUM);
+  // split K while the output tiles leave most SMs idle and each slice keeps
+  // at least one 64-wide step
+  int S = 1;
+  const int64_t tiles = (int64_t)grid.x * grid.y;
+  while (split_ws && tiles * S * 2 <= (int64_t)num_sms() * 2 && K / (S * 2) >= kUK &&
+         (size_t)S * 2 * M * N <= split_floats)
+    S *= 2;
+  if (S > 1) {
+    g.partial = split_ws;
+    g.k_split = ((K + S - 1) / S + kUK - 1) / kUK * kUK;
+    S = (K + g.k_split - 1) / g.k_split;
+    grid.z = S;
+  }
   umma_gemm_kernel<<<grid, 128, kUmmaSmem, s>>>(g);
+  cudaError_t r = cudaGetLastError();
+  if (r != cudaSuccess || S == 1) return r;
+  splitk_reduce_kernel<<<(unsigned)(((int64_t)M * N + 255) / 256), 256, 0, s>>>(g, S);
   return cudaGetLastError();
 }
 

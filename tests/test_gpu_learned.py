@@ -169,3 +169,40 @@ def test_training_reduces_loss_and_beats_the_prior(ppl, orc):
         ess_p.append(prior[b]["ess"])
     assert np.median(ess_l) > 10 * np.median(ess_p), (np.median(ess_l), np.median(ess_p))
     assert np.mean(np.array(err_l) < 0.05) > np.mean(np.array(err_p) < 0.05)
+
+
+def test_training_steps_replayed_from_a_cuda_graph_match_direct_training(ppl):
+    # one block of 16 steps captured once and replayed three times trains the
+    # network exactly as 48 steps of ppl_proposal_train (the steps read their
+    # pair range and loss slot from the device step counter)
+    import torch
+    model = ppl.poly_model()
+    n_pairs, batch, epochs, seed = 1 << 14, 1024, 3, 77
+    steps = epochs * (n_pairs // batch)
+    W = synth.mlp_weights(3)
+
+    def fresh():
+        p = ppl.pack_params(W)
+        return p, torch.zeros_like(p), torch.zeros_like(p)
+    pa, ma, va = fresh()
+    la = torch.zeros(steps, dtype=torch.float64, device="cuda")
+    ppl.ppl_proposal_train(model, pa, ma, va, n_pairs, batch, epochs, seed, 1e-3, la)
+    # warm-up on scratch buffers (first-call set-up happens outside the capture)
+    ps, ms, vs = fresh()
+    ws = ppl.proposal_workspace(batch)
+    ppl.ppl_proposal_train_init(ps, batch, ws)
+    ppl.ppl_proposal_train_steps(model, ps, ms, vs, n_pairs, batch, 1, seed, 1e-3, None, ws)
+    torch.cuda.synchronize()
+    pb, mb, vb = fresh()
+    lb = torch.zeros(steps, dtype=torch.float64, device="cuda")
+    ppl.ppl_proposal_train_init(pb, batch, ws)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        ppl.ppl_proposal_train_steps(model, pb, mb, vb, n_pairs, batch, 16, seed, 1e-3, lb, ws)
+    for _ in range(steps // 16):
+        g.replay()
+    torch.cuda.synchronize()
+    assert ppl.ppl_workspace_status(ws) == 0
+    assert torch.equal(pb, pa) and torch.equal(mb, ma) and torch.equal(vb, va)
+    assert torch.allclose(lb, la, rtol=1e-12, atol=0.0)
