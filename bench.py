@@ -46,10 +46,10 @@ KERNELS_PER_STEP = 2  # trace (normalisation and posterior fused), resampling (g
 # a kernel changed since its capture reports traffic null instead of a stale
 # number.
 MEASURED_TRAFFIC = {
-    "poly_trace_tc_kernel": {"bytes": 163330 + 541910000, "source": "trace_tc.cu",
-                             "sha256": "df40aa9872af14d1"},
-    "resample_coop_kernel": {"bytes": 67370000 + 538910000, "source": "resample_coop.cu",
-                             "sha256": "2bcd3b331248d2cc"},
+    "poly_trace_tc_kernel": {"bytes": 245248 + 538769408, "source": "trace_tc.cu",
+                             "sha256": "d1b865959934003f"},
+    "resample_coop_kernel": {"bytes": 68295424 + 546867456, "source": "resample_coop.cu",
+                             "sha256": "048ef78ecca62396"},
 }
 
 
