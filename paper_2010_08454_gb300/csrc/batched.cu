@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(kTpb, PPT >= 8 ? 2 : (LEARNED ? 3 : 4)) batche
   TraceSmem<PPT>& ts = *reinterpret_cast<TraceSmem<PPT>*>(smem);
   float2* sdata = reinterpret_cast<float2*>(smem + trace_smem_bytes<PPT>());
   __shared__ DegPartial gout[kMaxDegrees], fin[kMaxDegrees];
-  __shared__ double fS[kMaxDegrees], fS2[kMaxDegrees];
+  __shared__ float2 fS[kMaxDegrees], fS2[kMaxDegrees];
   __shared__ int64_t item_sh;
   __shared__ bool last_sh;
   __shared__ ProposalSmem prop;
@@ -154,41 +154,18 @@ __global__ void __launch_bounds__(kTpb, PPT >= 8 ? 2 : (LEARNED ? 3 : 4)) batche
       const int64_t np = ni * (kTpb / 32);  // (tile, warp) partials per degree
       if (warp < kMaxDegrees) {
         DegPartial a;
-        deg_empty(a);
-        for (int64_t j = lane; j < np; j += 32) {
-          const DegPartial q = ld_partial_cg(parts + (i0 * (kTpb / 32) + j) * kMaxDegrees + warp);
-          deg_merge(a, q);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const DegPartial other = deg_shfl_xor(a, o);
-          deg_merge(a, other);
-        }
-        double s = 0.0, s2 = 0.0;
-        if (a.m != -INFINITY) {
-          for (int64_t j = lane; j < np; j += 32) {
-            const DegPartial q = ld_partial_cg(parts + (i0 * (kTpb / 32) + j) * kMaxDegrees + warp);
-            if (q.m == -INFINITY) continue;
-            const double e = (double)expf(q.m - a.m);
-            s += (double)q.S * e;
-            s2 += (double)q.S2 * e * e;
-          }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          s += __shfl_xor_sync(0xffffffffu, s, o);
-          s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        }
+        DegSums ds;
+        merge_degree(parts + i0 * (kTpb / 32) * kMaxDegrees, (int)np, warp, lane, a, ds);
         if (lane == 0) {
           fin[warp] = a;
-          fS[warp] = s;
-          fS2[warp] = s2;
+          fS[warp] = ds.S;
+          fS2[warp] = ds.S2;
         }
       }
       __syncthreads();
-      if (tid == 0)
-        write_summary(fin, fS, fS2, p.n_deg, p.min_deg, N, ld_volatile_i32(&hdr->status),
-                      out + b);
+      if (warp == 0)
+        write_summary_warp(fin, fS, fS2, p.n_deg, p.min_deg, N,
+                           lane == 0 ? ld_volatile_i32(&hdr->status) : 0, out + b);
       __syncthreads();
     }
   }

@@ -6,6 +6,7 @@
 #include <map>
 #include <mutex>
 
+#include "dfloat.cuh"
 #include "kernels.h"
 #include "poly.cuh"
 #include "posterior.cuh"
@@ -253,11 +254,12 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float v) {
 // Final merge by the last block: the maximum and its lowest index in FP32
 // (exact), then every partial's sums rescaled to the merged maximum (FP32
 // exp of a difference of two floats) and added in double-float per lane,
-// combined across lanes and warps in FP64; thread 0 writes the results.
+// across lanes and across warps; thread 0 takes log s by df_log and the ESS
+// as a corrected quotient (no FP64 arithmetic but the final addition).
 __device__ __forceinline__ void lse_finalize(const StatPartial* parts, int G, int64_t N,
                                              WsHeader* hdr, double* lse_out) {
   __shared__ float M_sh;
-  __shared__ double wsum[kStatThreads / 32][2];
+  __shared__ float2 wsum[kStatThreads / 32][2];
   LseAcc a;
   a.init();
   for (int b = threadIdx.x; b < G; b += kStatThreads) {
@@ -284,12 +286,8 @@ __device__ __forceinline__ void lse_finalize(const StatPartial* parts, int G, in
       df_add(qh, ql, parts[b].s2 * e * e);
     }
   }
-  double s = (double)sh + (double)sl, s2 = (double)qh + (double)ql;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    s += __shfl_xor_sync(0xffffffffu, s, o);
-    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-  }
+  float2 s = df_warp_sum(df_add(make_float2(sh, 0.0f), make_float2(sl, 0.0f)));
+  float2 s2 = df_warp_sum(df_add(make_float2(qh, 0.0f), make_float2(ql, 0.0f)));
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (lane == 0) {
     wsum[warp][0] = s;
@@ -297,19 +295,22 @@ __device__ __forceinline__ void lse_finalize(const StatPartial* parts, int G, in
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    s = 0.0;
-    s2 = 0.0;
+    s = wsum[0][0];
+    s2 = wsum[0][1];
 #pragma unroll
-    for (int w = 0; w < kStatThreads / 32; ++w) {
-      s += wsum[w][0];
-      s2 += wsum[w][1];
+    for (int w = 1; w < kStatThreads / 32; ++w) {
+      s = df_add(s, wsum[w][0]);
+      s2 = df_add(s2, wsum[w][1]);
     }
     int32_t code = 0;
     if (r.nan) code = PPL_ENAN;
     else if (!(M > -INFINITY)) code = PPL_EEMPTY;
     if (code) record_status(&hdr->status, code);
-    const double lse = (double)M + log(s);
-    const double ess = s * s / s2;
+    double lse = -INFINITY, ess = nan("");
+    if (s.x > 0.0f) {
+      lse = (double)M + df_to_double(df_log(s));
+      ess = (double)df_div(df_mul(s, s), s2);
+    }
     hdr->max_lw = M;
     hdr->lse = lse;
     hdr->ess = ess;

@@ -13,6 +13,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "poly.cuh"
 
 namespace ppl {
@@ -232,57 +233,115 @@ __device__ __forceinline__ void group_partial(const float (&lw)[PPT], const int 
   __syncthreads();
 }
 
-// Summary of a population from its four per-degree partials, in FP64.
-// S and S2 are the per-degree sums already combined in FP64 by the caller.
-__device__ __forceinline__ void write_summary(const DegPartial (&p)[kMaxDegrees],
-                                              const double (&S)[kMaxDegrees],
-                                              const double (&S2)[kMaxDegrees], int n_deg,
-                                              int min_deg, int64_t N, int32_t status,
-                                              ppl_is_result* res) {
-  double M = -INFINITY;
-  int64_t arg = -1;
+// Summary of a population from its four per-degree partials, by the 32 lanes
+// of one warp (every lane calls it).  S and S2 are the per-degree sums around
+// each degree's maximum as double-floats.  The degree masses, log Z, p(n) and
+// the ESS are FP64 (a degree's mass may lie far below FP32's range), but
+// GB300's FP64 pipe is narrow and slow, so the work is spread over the lanes
+// and every lane's chain of FP64 operations is short: lanes 0-3 take one
+// degree's mass (an exp), lane 0 log(s), lane 1 log(N), lane 2 the ESS, lanes
+// 0-23 one (degree, coefficient) variance each, lanes 0-5 one pooled mean.
+__device__ __forceinline__ void write_summary_warp(const DegPartial (&p)[kMaxDegrees],
+                                                   const float2 (&S)[kMaxDegrees],
+                                                   const float2 (&S2)[kMaxDegrees], int n_deg,
+                                                   int min_deg, int64_t N, int32_t status,
+                                                   ppl_is_result* res) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  // the best trace (FP32 compares: the conversion to FP64 is exact and monotone)
+  float Mf = -INFINITY;
+  int32_t arg = -1;
   for (int k = 0; k < n_deg; ++k)
-    if (p[k].m != -INFINITY &&
-        ((double)p[k].m > M || ((double)p[k].m == M && p[k].arg < arg))) {
-      M = p[k].m;
+    if (p[k].m != -INFINITY && (p[k].m > Mf || (p[k].m == Mf && p[k].arg < arg))) {
+      Mf = p[k].m;
       arg = p[k].arg;
     }
-  double s = 0.0, s2 = 0.0, mass[kMaxDegrees];
-  for (int k = 0; k < kMaxDegrees; ++k) {
-    mass[k] = 0.0;
-    if (k < n_deg && p[k].m != -INFINITY && S[k] > 0.0) {
-      const double e = exp((double)p[k].m - M);
-      mass[k] = e * S[k];
-      s += mass[k];
-      s2 += e * e * S2[k];
-    }
+  const double M = (double)Mf;
+  // lanes 0-3: degree `lane`'s mass e S and e^2 S2 around the best trace
+  const int kd = lane & 3;
+  const bool has_k = lane < kMaxDegrees && kd < n_deg && p[kd].m != -INFINITY;
+  double mass = 0.0, q2 = 0.0;
+  if (has_k && S[kd].x > 0.0f) {
+    const double e = exp((double)p[kd].m - M);
+    mass = e * df_to_double(S[kd]);
+    q2 = e * e * df_to_double(S2[kd]);
   }
-  res->lse = M + log(s);
-  res->log_z = res->lse - log((double)N);
-  res->ess = s * s / s2;
-  res->max_lw = M;
-  res->argmax = arg;
-  res->n_particles = N;
-  res->n_deg = n_deg;
-  int best = 0;
-  for (int j = 0; j < kMaxCoef; ++j) res->mean_c[j] = 0.0;
+  double s = 0.0, s2 = 0.0;
+#pragma unroll
   for (int k = 0; k < kMaxDegrees; ++k) {
-    const bool has = k < n_deg && p[k].m != -INFINITY;
-    const double pn = s > 0.0 ? mass[k] / s : 0.0;
-    res->p_n[k] = pn;
-    if (k < n_deg && pn > res->p_n[best]) best = k;
-    res->deg_max_lw[k] = has ? (double)p[k].m : -INFINITY;
-    res->deg_argmax[k] = has ? p[k].arg : -1;
-    for (int j = 0; j < kMaxCoef; ++j) {
-      const bool ok = has && S[k] > 0.0 && p[k].S > 0.0f;
-      res->deg_mean[k][j] = ok ? (double)p[k].mean[j] : 0.0;
-      res->deg_var[k][j] = ok ? (double)p[k].M2[j] / (double)p[k].S : 0.0;
-      res->mean_c[j] += pn * res->deg_mean[k][j];
-    }
+    s += __shfl_sync(full, mass, k);
+    s2 += __shfl_sync(full, q2, k);
   }
-  res->map_deg = min_deg + best;
-  res->status = status;
+  // lane 0: log(s); lane 1: log(N); lane 2: the ESS
+  double t = 0.0;
+  if (lane == 0) t = log(s);
+  else if (lane == 1) t = log((double)N);
+  else if (lane == 2) t = s * s / s2;
+  const double log_s = __shfl_sync(full, t, 0), log_n = __shfl_sync(full, t, 1);
+  const double ess = __shfl_sync(full, t, 2);
+  // lanes 0-3: the degree masses p(n)
+  const double pn = (lane < kMaxDegrees && s > 0.0) ? mass / s : 0.0;
+  double pns[kMaxDegrees];
+#pragma unroll
+  for (int k = 0; k < kMaxDegrees; ++k) pns[k] = __shfl_sync(full, pn, k);
+  // lanes 0-23: (degree k, coefficient j) mean and variance
+  if (lane < kMaxDegrees * kMaxCoef) {
+    const int k = lane / kMaxCoef, j = lane % kMaxCoef;
+    const bool ok = k < n_deg && p[k].m != -INFINITY && S[k].x > 0.0f && p[k].S > 0.0f;
+    res->deg_mean[k][j] = ok ? (double)p[k].mean[j] : 0.0;
+    res->deg_var[k][j] = ok ? (double)p[k].M2[j] / (double)p[k].S : 0.0;
+  }
+  // lanes 0-5: pooled coefficient means, summed over degrees in order
+  if (lane < kMaxCoef) {
+    double mc = 0.0;
+#pragma unroll
+    for (int k = 0; k < kMaxDegrees; ++k) {
+      const bool ok = k < n_deg && p[k].m != -INFINITY && S[k].x > 0.0f && p[k].S > 0.0f;
+      mc += pns[k] * (ok ? (double)p[k].mean[lane] : 0.0);
+    }
+    res->mean_c[lane] = mc;
+  }
+  if (lane < kMaxDegrees) {
+    res->p_n[lane] = pn;
+    res->deg_max_lw[lane] = has_k ? (double)p[lane].m : -INFINITY;
+    res->deg_argmax[lane] = has_k ? p[lane].arg : -1;
+  }
+  if (lane == 0) {
+    int best = 0;
+    for (int k = 1; k < n_deg; ++k)
+      if (pns[k] > pns[best]) best = k;
+    res->lse = M + log_s;
+    res->log_z = res->lse - log_n;
+    res->ess = ess;
+    res->max_lw = M;
+    res->argmax = arg;
+    res->n_particles = N;
+    res->n_deg = n_deg;
+    res->map_deg = min_deg + best;
+    res->status = status;
+  }
 }
+
+// A degree's sums S, S2 over partials q rescaled to the merged maximum M
+// (FP32 exp of the difference, double-float products and sums), added by the
+// lanes of a warp; every lane gets the totals.
+struct DegSums {
+  float2 S, S2;
+  __device__ __forceinline__ void zero() {
+    S = make_float2(0.0f, 0.0f);
+    S2 = make_float2(0.0f, 0.0f);
+  }
+  __device__ __forceinline__ void add(float qm, float2 qS, float2 qS2, float M) {
+    if (qm == -INFINITY) return;
+    const float e = expf(qm - M);
+    S = df_add(S, df_mul(qS, e));
+    S2 = df_add(S2, df_mul(df_mul(qS2, e), e));
+  }
+  __device__ __forceinline__ void warp_total() {
+    S = df_warp_sum(S);
+    S2 = df_warp_sum(S2);
+  }
+};
 
 // ---------------------------------------------------------------------------
 // Final merge of the per-block partials, by the last block: warp k merges
@@ -290,49 +349,73 @@ __device__ __forceinline__ void write_summary(const DegPartial (&p)[kMaxDegrees]
 // sums S, S2 are recombined in FP64 around the merged maximum; thread 0
 // writes the summary.
 // ---------------------------------------------------------------------------
+// Warp `warp` (< kMaxDegrees) merges degree `warp` of G block partials: the
+// maximum, its index and the moments in FP32 (a lane-strided chain, then a
+// shuffle tree), then the sums S, S2 rescaled to the merged maximum.
+__device__ __forceinline__ void merge_degree(const DegPartial* parts, int G, int warp, int lane,
+                                             DegPartial& a, DegSums& ds) {
+  // the partials come from L2 (written by other blocks of the running
+  // kernel); several loads are in flight per lane, since one round trip to L2
+  // costs about a microsecond here
+  constexpr int U = 4, V = 8;
+  deg_empty(a);
+  for (int b0 = lane; b0 < G; b0 += 32 * U) {
+    DegPartial q[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (b0 + 32 * u < G) q[u] = ld_partial_cg(parts + (b0 + 32 * u) * kMaxDegrees + warp);
+      else deg_empty(q[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) deg_merge(a, q[u]);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const DegPartial other = deg_shfl_xor(a, o);
+    deg_merge(a, other);
+  }
+  ds.zero();
+  if (a.m != -INFINITY)
+    for (int b0 = lane; b0 < G; b0 += 32 * V) {
+      float4 h[V];  // (m, arg, S, S2) of each partial
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        h[v] = b0 + 32 * v < G
+                   ? __ldcg(reinterpret_cast<const float4*>(parts + (b0 + 32 * v) * kMaxDegrees + warp))
+                   : make_float4(-INFINITY, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        ds.add(h[v].x, make_float2(h[v].z, 0.0f), make_float2(h[v].w, 0.0f), a.m);
+    }
+  ds.warp_total();
+}
+
 __device__ __forceinline__ void finalize_partials(const DegPartial* parts, int G, int n_deg,
                                                   int min_deg, int64_t N, WsHeader* hdr,
                                                   ppl_is_result* res) {
   __shared__ DegPartial fin[kMaxDegrees];
-  __shared__ double fS[kMaxDegrees], fS2[kMaxDegrees];
+  __shared__ float2 fS[kMaxDegrees], fS2[kMaxDegrees];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp < kMaxDegrees) {
     DegPartial a;
-    deg_empty(a);
-    for (int b = lane; b < G; b += 32) deg_merge(a, parts[b * kMaxDegrees + warp]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const DegPartial other = deg_shfl_xor(a, o);
-      deg_merge(a, other);
-    }
-    const float M = a.m;
-    double s = 0.0, s2 = 0.0;
-    if (M != -INFINITY) {
-      for (int b = lane; b < G; b += 32) {
-        const DegPartial& q = parts[b * kMaxDegrees + warp];
-        if (q.m == -INFINITY) continue;
-        const double e = (double)expf(q.m - M);
-        s += (double)q.S * e;
-        s2 += (double)q.S2 * e * e;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s += __shfl_xor_sync(0xffffffffu, s, o);
-      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    }
+    DegSums ds;
+    merge_degree(parts, G, warp, lane, a, ds);
     if (lane == 0) {
       fin[warp] = a;
-      fS[warp] = s;
-      fS2[warp] = s2;
+      fS[warp] = ds.S;
+      fS2[warp] = ds.S2;
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    bool any = false;
-    for (int k = 0; k < n_deg; ++k) any |= fin[k].m != -INFINITY;
-    if (!any) record_status(&hdr->status, PPL_EEMPTY);
-    if (res) write_summary(fin, fS, fS2, n_deg, min_deg, N, ld_volatile_i32(&hdr->status), res);
+  if (warp == 0) {
+    int32_t st = 0;
+    if (lane == 0) {
+      bool any = false;
+      for (int k = 0; k < n_deg; ++k) any |= fin[k].m != -INFINITY;
+      if (!any) record_status(&hdr->status, PPL_EEMPTY);
+      st = ld_volatile_i32(&hdr->status);
+    }
+    if (res) write_summary_warp(fin, fS, fS2, n_deg, min_deg, N, st, res);
   }
 }
 
@@ -347,7 +430,7 @@ __device__ __forceinline__ void finalize_partials(const DegPartial* parts, int G
 // ---------------------------------------------------------------------------
 struct __align__(16) IsPartial {
   DegPartial deg[kMaxDegrees];
-  double S[kMaxDegrees], S2[kMaxDegrees];
+  float2 S[kMaxDegrees], S2[kMaxDegrees];  // double-float sums around each degree's maximum
   int64_t n;
   int32_t status, n_deg, min_deg, pad0;
   unsigned char pad[32];
@@ -362,33 +445,12 @@ __device__ __forceinline__ void finalize_to_partial(const DegPartial* parts, int
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   if (warp < kMaxDegrees) {
     DegPartial a;
-    deg_empty(a);
-    for (int b = lane; b < G; b += 32) deg_merge(a, parts[b * kMaxDegrees + warp]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const DegPartial other = deg_shfl_xor(a, o);
-      deg_merge(a, other);
-    }
-    const float M = a.m;
-    double s = 0.0, s2 = 0.0;
-    if (M != -INFINITY) {
-      for (int b = lane; b < G; b += 32) {
-        const DegPartial& q = parts[b * kMaxDegrees + warp];
-        if (q.m == -INFINITY) continue;
-        const double e = (double)expf(q.m - M);
-        s += (double)q.S * e;
-        s2 += (double)q.S2 * e * e;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s += __shfl_xor_sync(0xffffffffu, s, o);
-      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    }
+    DegSums ds;
+    merge_degree(parts, G, warp, lane, a, ds);
     if (lane == 0) {
       out->deg[warp] = a;
-      out->S[warp] = s;
-      out->S2[warp] = s2;
+      out->S[warp] = ds.S;
+      out->S2[warp] = ds.S2;
     }
   }
   if (threadIdx.x == 0) {
@@ -402,11 +464,11 @@ __device__ __forceinline__ void finalize_to_partial(const DegPartial* parts, int
 // Merge of P shard partials into the summary of the whole population, by one
 // block: warp k merges degree k (the maxima exactly, means and second
 // moments by the parallel rule in FP32, the sums rescaled to the merged
-// maximum in FP64).  N is the total particle count.
+// maximum in double-float).  N is the total particle count.
 __device__ __forceinline__ void merge_shard_partials(const IsPartial* parts, int P, int64_t N,
                                                      int32_t status, ppl_is_result* res) {
   __shared__ DegPartial fin[kMaxDegrees];
-  __shared__ double fS[kMaxDegrees], fS2[kMaxDegrees];
+  __shared__ float2 fS[kMaxDegrees], fS2[kMaxDegrees];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int n_deg = parts[0].n_deg, min_deg = parts[0].min_deg;
   if (warp < kMaxDegrees) {
@@ -418,36 +480,26 @@ __device__ __forceinline__ void merge_shard_partials(const IsPartial* parts, int
       const DegPartial other = deg_shfl_xor(a, o);
       deg_merge(a, other);
     }
-    const float M = a.m;
-    double s = 0.0, s2 = 0.0;
-    if (M != -INFINITY) {
-      for (int g = lane; g < P; g += 32) {
-        const float m = parts[g].deg[warp].m;
-        if (m == -INFINITY) continue;
-        const double e = (double)expf(m - M);
-        s += parts[g].S[warp] * e;
-        s2 += parts[g].S2[warp] * e * e;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      s += __shfl_xor_sync(0xffffffffu, s, o);
-      s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-    }
+    DegSums ds;
+    ds.zero();
+    if (a.m != -INFINITY)
+      for (int g = lane; g < P; g += 32)
+        ds.add(parts[g].deg[warp].m, parts[g].S[warp], parts[g].S2[warp], a.m);
+    ds.warp_total();
     if (lane == 0) {
       fin[warp] = a;
-      fS[warp] = s;
-      fS2[warp] = s2;
+      fS[warp] = ds.S;
+      fS2[warp] = ds.S2;
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (warp == 0) {
     int32_t st = status;
     for (int g = 0; g < P && st == 0; ++g) st = parts[g].status;
     bool any = false;
     for (int k = 0; k < n_deg; ++k) any |= fin[k].m != -INFINITY;
     if (st == 0 && !any) st = PPL_EEMPTY;
-    write_summary(fin, fS, fS2, n_deg, min_deg, N, st, res);
+    write_summary_warp(fin, fS, fS2, n_deg, min_deg, N, st, res);
   }
 }
 

@@ -22,6 +22,7 @@
 // resident at once (or fails to launch).
 #include <algorithm>
 
+#include "dfloat.cuh"
 #include "gridsync.cuh"
 #include "kernels.h"
 #include "rng.cuh"
@@ -58,34 +59,6 @@ struct __align__(128) SmcCtl {
   GridCtl g;
 };
 
-// Double-float arithmetic (pairs hi + lo, |lo| <= ulp(hi) / 2): Knuth's
-// TwoSum for the sum, an FMA-exact product (Dekker's TwoProduct).  The
-// per-step sums stay off the FP64 pipe, which is narrow on this GPU.
-__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
-  const float s = __fadd_rn(a.x, b.x);
-  const float bb = __fsub_rn(s, a.x);
-  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
-  const float t = __fadd_rn(e, __fadd_rn(a.y, b.y));
-  const float hi = __fadd_rn(s, t);
-  return make_float2(hi, __fsub_rn(t, __fsub_rn(hi, s)));
-}
-__device__ __forceinline__ float2 df_prod(float a, float b) {
-  const float p = __fmul_rn(a, b);
-  return make_float2(p, __fmaf_rn(a, b, -p));
-}
-__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
-  float2 p = df_prod(a.x, b.x);
-  p.y = __fmaf_rn(a.x, b.y, __fmaf_rn(a.y, b.x, p.y));
-  const float hi = __fadd_rn(p.x, p.y);
-  return make_float2(hi, __fsub_rn(p.y, __fsub_rn(hi, p.x)));
-}
-__device__ __forceinline__ float2 df_warp_sum(float2 v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1)
-    v = df_add(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, o),
-                              __shfl_xor_sync(0xffffffffu, v.y, o)));
-  return v;
-}
 struct SmcArgs {
   LgssmParams p;
   const float* y;  // [T]
