@@ -80,4 +80,23 @@ __device__ __forceinline__ float2 df_log(float2 x) {
   return make_float2(s, __fsub_rn(lo, __fsub_rn(s, hi)));
 }
 
+// e^d for an FP32 d <= 0 as 2^n m, with n an integer and m = e^r, r in
+// [-ln2/2, ln2/2] (Cody and Waite's reduction r = d - n ln2, ln 2 split as
+// above so n hi is exact for |n| < 512): m keeps FP32's relative precision
+// where e^d itself lies far below FP32's range.  d < -1000 (below FP64's
+// range too) gives m = 0.
+struct ExpSplit {
+  int n;
+  float m;
+};
+__device__ __forceinline__ ExpSplit exp_split(float d) {
+  if (!(d >= -1000.0f)) return ExpSplit{0, 0.0f};
+  const float n = rintf(__fmul_rn(d, 1.44269504f));
+  const float r = __fmaf_rn(-n, 0x1.7f7d1cp-20f, __fmaf_rn(-n, 0x1.62e4p-1f, d));
+  return ExpSplit{(int)n, expf(r)};
+}
+
+// 2^n as an FP32 value, for n in [-126, 127].
+__device__ __forceinline__ float exp2i(int n) { return __int_as_float((127 + n) << 23); }
+
 }  // namespace ppl

@@ -235,85 +235,101 @@ __device__ __forceinline__ void group_partial(const float (&lw)[PPT], const int 
 
 // Summary of a population from its four per-degree partials, by the 32 lanes
 // of one warp (every lane calls it).  S and S2 are the per-degree sums around
-// each degree's maximum as double-floats.  The degree masses, log Z, p(n) and
-// the ESS are FP64 (a degree's mass may lie far below FP32's range), but
-// GB300's FP64 pipe is narrow and slow, so the work is spread over the lanes
-// and every lane's chain of FP64 operations is short: lanes 0-3 take one
-// degree's mass (an exp), lane 0 log(s), lane 1 log(N), lane 2 the ESS, lanes
-// 0-23 one (degree, coefficient) variance each, lanes 0-5 one pooled mean.
+// each degree's maximum as double-floats.  No FP64 arithmetic but single
+// conversions and power-of-two scalings (GB300's FP64 pipe is narrow: a chain
+// of FP64 exp, log and divisions took about 7 us): the degree weights
+// e^(m_k - M) = 2^n_k w_k (exp_split, so a degree's mass keeps its relative
+// precision far below FP32's range), the masses w_k S_k and their total s in
+// double-float, log s by df_log, p(n) and the ESS as corrected FP32 quotients
+// scaled back by 2^n_k in FP64.  Lanes 0-23 take one (degree, coefficient)
+// variance each, lanes 0-5 one pooled mean each.
 __device__ __forceinline__ void write_summary_warp(const DegPartial (&p)[kMaxDegrees],
                                                    const float2 (&S)[kMaxDegrees],
                                                    const float2 (&S2)[kMaxDegrees], int n_deg,
                                                    int min_deg, int64_t N, int32_t status,
                                                    ppl_is_result* res) {
-  const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  // the best trace (FP32 compares: the conversion to FP64 is exact and monotone)
-  float Mf = -INFINITY;
+  float M = -INFINITY;
   int32_t arg = -1;
   for (int k = 0; k < n_deg; ++k)
-    if (p[k].m != -INFINITY && (p[k].m > Mf || (p[k].m == Mf && p[k].arg < arg))) {
-      Mf = p[k].m;
+    if (p[k].m != -INFINITY && (p[k].m > M || (p[k].m == M && p[k].arg < arg))) {
+      M = p[k].m;
       arg = p[k].arg;
     }
-  const double M = (double)Mf;
-  // lanes 0-3: degree `lane`'s mass e S and e^2 S2 around the best trace
-  const int kd = lane & 3;
-  const bool has_k = lane < kMaxDegrees && kd < n_deg && p[kd].m != -INFINITY;
-  double mass = 0.0, q2 = 0.0;
-  if (has_k && S[kd].x > 0.0f) {
-    const double e = exp((double)p[kd].m - M);
-    mass = e * df_to_double(S[kd]);
-    q2 = e * e * df_to_double(S2[kd]);
-  }
-  double s = 0.0, s2 = 0.0;
+  // degree k's mass 2^n[k] mw[k] and e^(2 (m_k - M)) S2_k; s, s2 their totals
+  // (terms below 2^-120 of the best degree's, which is at least 1, vanish
+  // at double-float precision)
+  int n[kMaxDegrees];
+  float2 mw[kMaxDegrees];
+  float2 s = make_float2(0.0f, 0.0f), s2 = make_float2(0.0f, 0.0f);
 #pragma unroll
   for (int k = 0; k < kMaxDegrees; ++k) {
-    s += __shfl_sync(full, mass, k);
-    s2 += __shfl_sync(full, q2, k);
+    n[k] = 0;
+    mw[k] = make_float2(0.0f, 0.0f);
+    if (k < n_deg && p[k].m != -INFINITY && S[k].x > 0.0f) {
+      // m_k - M = dh + dl exactly (TwoSum of two floats); e^dl = 1 + dl
+      const float dh = __fsub_rn(p[k].m, M);
+      const float bb = __fsub_rn(dh, p[k].m);
+      const float dl = __fsub_rn(__fsub_rn(p[k].m, __fsub_rn(dh, bb)), __fadd_rn(M, bb));
+      const ExpSplit e = exp_split(dh);
+      const float2 w = df_add(make_float2(e.m, 0.0f), make_float2(__fmul_rn(e.m, dl), 0.0f));
+      n[k] = e.n;
+      mw[k] = df_mul(S[k], w);
+      if (e.n >= -120) {
+        s = df_add(s, df_mul(mw[k], exp2i(e.n)));
+        if (e.n >= -60) s2 = df_add(s2, df_mul(df_mul(df_mul(S2[k], w), w), exp2i(2 * e.n)));
+      }
+    }
   }
-  // lane 0: log(s); lane 1: log(N); lane 2: the ESS
-  double t = 0.0;
-  if (lane == 0) t = log(s);
-  else if (lane == 1) t = log((double)N);
-  else if (lane == 2) t = s * s / s2;
-  const double log_s = __shfl_sync(full, t, 0), log_n = __shfl_sync(full, t, 1);
-  const double ess = __shfl_sync(full, t, 2);
-  // lanes 0-3: the degree masses p(n)
-  const double pn = (lane < kMaxDegrees && s > 0.0) ? mass / s : 0.0;
-  double pns[kMaxDegrees];
+  // p(n): the FP32 quotient mw / s scaled by 2^n (FP32 value for the pooled
+  // means, FP64 for the output)
+  float pf[kMaxDegrees], pq[kMaxDegrees];
 #pragma unroll
-  for (int k = 0; k < kMaxDegrees; ++k) pns[k] = __shfl_sync(full, pn, k);
+  for (int k = 0; k < kMaxDegrees; ++k) {
+    pq[k] = (s.x > 0.0f && mw[k].x > 0.0f) ? df_div(mw[k], s) : 0.0f;
+    pf[k] = n[k] >= -120 ? __fmul_rn(pq[k], exp2i(n[k])) : 0.0f;
+  }
   // lanes 0-23: (degree k, coefficient j) mean and variance
   if (lane < kMaxDegrees * kMaxCoef) {
     const int k = lane / kMaxCoef, j = lane % kMaxCoef;
     const bool ok = k < n_deg && p[k].m != -INFINITY && S[k].x > 0.0f && p[k].S > 0.0f;
     res->deg_mean[k][j] = ok ? (double)p[k].mean[j] : 0.0;
-    res->deg_var[k][j] = ok ? (double)p[k].M2[j] / (double)p[k].S : 0.0;
+    res->deg_var[k][j] = ok ? (double)__fdiv_rn(p[k].M2[j], p[k].S) : 0.0;
   }
-  // lanes 0-5: pooled coefficient means, summed over degrees in order
+  // lanes 0-5: pooled coefficient means
   if (lane < kMaxCoef) {
-    double mc = 0.0;
+    float2 mc = make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int k = 0; k < kMaxDegrees; ++k) {
       const bool ok = k < n_deg && p[k].m != -INFINITY && S[k].x > 0.0f && p[k].S > 0.0f;
-      mc += pns[k] * (ok ? (double)p[k].mean[lane] : 0.0);
+      if (ok) mc = df_add(mc, df_prod(pf[k], p[k].mean[lane]));
     }
-    res->mean_c[lane] = mc;
+    res->mean_c[lane] = df_to_double(mc);
   }
   if (lane < kMaxDegrees) {
-    res->p_n[lane] = pn;
-    res->deg_max_lw[lane] = has_k ? (double)p[lane].m : -INFINITY;
-    res->deg_argmax[lane] = has_k ? p[lane].arg : -1;
+    const int k = lane;
+    const bool has = k < n_deg && p[k].m != -INFINITY;
+    // 2^n as an FP64 value (n >= -1022; smaller masses underflow to 0)
+    const double scale = n[k] >= -1022 ? __hiloint2double((n[k] + 1023) << 20, 0) : 0.0;
+    res->p_n[k] = (double)pq[k] * scale;
+    res->deg_max_lw[k] = has ? (double)p[k].m : -INFINITY;
+    res->deg_argmax[k] = has ? p[k].arg : -1;
   }
   if (lane == 0) {
     int best = 0;
     for (int k = 1; k < n_deg; ++k)
-      if (pns[k] > pns[best]) best = k;
-    res->lse = M + log_s;
-    res->log_z = res->lse - log_n;
-    res->ess = ess;
-    res->max_lw = M;
+      if (pf[k] > pf[best]) best = k;
+    if (s.x > 0.0f) {
+      const float2 log_s = df_log(s), log_n = df_log(df_from_i64(N));
+      res->lse = (double)M + df_to_double(log_s);
+      res->log_z = (double)M + df_to_double(df_add(log_s, df_neg(log_n)));
+      res->ess = (double)df_div(df_mul(s, s), s2);
+    } else {  // no finite weight
+      res->lse = -INFINITY;
+      res->log_z = -INFINITY;
+      res->ess = nan("");
+    }
+    res->max_lw = (double)M;
     res->argmax = arg;
     res->n_particles = N;
     res->n_deg = n_deg;
@@ -338,55 +354,55 @@ struct DegSums {
     S2 = df_add(S2, df_mul(df_mul(qS2, e), e));
   }
   __device__ __forceinline__ void warp_total() {
-    S = df_warp_sum(S);
-    S2 = df_warp_sum(S2);
+#pragma unroll 1
+    for (int o = 16; o > 0; o >>= 1) {
+      S = df_add(S, df_shfl_xor(S, o));
+      S2 = df_add(S2, df_shfl_xor(S2, o));
+    }
   }
 };
 
 // ---------------------------------------------------------------------------
 // Final merge of the per-block partials, by the last block: warp k merges
 // degree k's partials (FP32, a lane-strided chain then a shuffle tree); the
-// sums S, S2 are recombined in FP64 around the merged maximum; thread 0
-// writes the summary.
+// sums S, S2 are recombined in double-float around the merged maximum; warp
+// 0 writes the summary.
 // ---------------------------------------------------------------------------
 // Warp `warp` (< kMaxDegrees) merges degree `warp` of G block partials: the
 // maximum, its index and the moments in FP32 (a lane-strided chain, then a
 // shuffle tree), then the sums S, S2 rescaled to the merged maximum.
 __device__ __forceinline__ void merge_degree(const DegPartial* parts, int G, int warp, int lane,
                                              DegPartial& a, DegSums& ds) {
-  // the partials come from L2 (written by other blocks of the running
-  // kernel); several loads are in flight per lane, since one round trip to L2
-  // costs about a microsecond here
-  constexpr int U = 4, V = 8;
+  // This code runs once per launch, by one block, after the kernel's data
+  // have streamed through L2: its instructions are fetched cold, so the loops
+  // stay rolled (fewer instruction fetches), and the next partial is loaded
+  // while the current one is merged.
   deg_empty(a);
-  for (int b0 = lane; b0 < G; b0 += 32 * U) {
-    DegPartial q[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (b0 + 32 * u < G) q[u] = ld_partial_cg(parts + (b0 + 32 * u) * kMaxDegrees + warp);
-      else deg_empty(q[u]);
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) deg_merge(a, q[u]);
+  DegPartial nxt;
+  if (lane < G) nxt = ld_partial_cg(parts + lane * kMaxDegrees + warp);
+#pragma unroll 1
+  for (int b = lane; b < G; b += 32) {
+    const DegPartial cur = nxt;
+    if (b + 32 < G) nxt = ld_partial_cg(parts + (b + 32) * kMaxDegrees + warp);
+    deg_merge(a, cur);
   }
-#pragma unroll
+#pragma unroll 1
   for (int o = 16; o > 0; o >>= 1) {
     const DegPartial other = deg_shfl_xor(a, o);
     deg_merge(a, other);
   }
   ds.zero();
-  if (a.m != -INFINITY)
-    for (int b0 = lane; b0 < G; b0 += 32 * V) {
-      float4 h[V];  // (m, arg, S, S2) of each partial
-#pragma unroll
-      for (int v = 0; v < V; ++v)
-        h[v] = b0 + 32 * v < G
-                   ? __ldcg(reinterpret_cast<const float4*>(parts + (b0 + 32 * v) * kMaxDegrees + warp))
-                   : make_float4(-INFINITY, 0.0f, 0.0f, 0.0f);
-#pragma unroll
-      for (int v = 0; v < V; ++v)
-        ds.add(h[v].x, make_float2(h[v].z, 0.0f), make_float2(h[v].w, 0.0f), a.m);
+  if (a.m != -INFINITY) {
+    float4 h = make_float4(-INFINITY, 0.0f, 0.0f, 0.0f);  // (m, arg, S, S2)
+    if (lane < G) h = __ldcg(reinterpret_cast<const float4*>(parts + lane * kMaxDegrees + warp));
+#pragma unroll 1
+    for (int b = lane; b < G; b += 32) {
+      const float4 cur = h;
+      if (b + 32 < G)
+        h = __ldcg(reinterpret_cast<const float4*>(parts + (b + 32) * kMaxDegrees + warp));
+      ds.add(cur.x, make_float2(cur.z, 0.0f), make_float2(cur.w, 0.0f), a.m);
     }
+  }
   ds.warp_total();
 }
 

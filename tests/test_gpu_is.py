@@ -95,6 +95,23 @@ def test_posterior_reduce_on_given_population(ppl, orc):
     assert out["ess"] == pytest.approx(N, rel=1e-6)
 
 
+def test_prior_draws_within_a_few_fp32_ulps_of_fp64(ppl, orc):
+    """Every coefficient is a Box-Muller normal computed in FP32 from the
+    trace's Philox words; against the FP64 normal of the same words it lies
+    within 1e-6 relative (a few FP32 ulps), also near the zeros of cos and sin
+    and for u_a near 1, where ln u_a is tiny (the FP32 functions keep their
+    relative precision there)."""
+    x, y = synth.poly_dataset(4, 1)
+    N = 1 << 20
+    kw = dict(min_deg=5, max_deg=5, coef_offset=1, prior_sigma=1.0)
+    res, lw, n, c, origin = gpu_is(ppl, x, y, N, 21, **kw)
+    _, (lw_r, n_r, c_r) = orc.infer_is_poly(orc.poly_model(**kw), x, y, N, 21)
+    assert np.array_equal(n, n_r)
+    rel = np.abs(c.astype(np.float64) - c_r) / np.abs(c_r)
+    print("max relative error of the FP32 normals:", float(rel.max()))
+    assert float(rel.max()) <= 1e-6
+
+
 def test_rng_words_bit_exact(ppl, orc):
     for seed, inst, step, purpose in [(0, 0, 0, 1), (0x0123456789ABCDEF, 3, 11, 2), (7, 0, 5, 3)]:
         w = ppl.ppl_rng_words(seed, inst, step, purpose, 300, 3).cpu().numpy().view(np.uint32)
