@@ -167,7 +167,7 @@ ppl_status ppl_infer_is_instance(const ppl_model* model, const ppl_data* data,
   PPL_TRY(check_ws(ws, ws_bytes, n_particles, data->len, &w));
   cudaStream_t s = (cudaStream_t)stream;
   PPL_TRY(reset_ws(w, false, s));
-  PPL_TRY(cuda_status(cudaMemsetAsync(out_dev, 0, sizeof(ppl_is_result), s)));
+  // (the last block writes every field of *out_dev)
   // the polynomial evaluations on the tensor cores while the data set fits in
   // shared memory, in FP32 on the CUDA cores beyond
   if (data->len <= trace_tc_max_points())

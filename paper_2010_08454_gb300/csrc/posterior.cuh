@@ -335,6 +335,7 @@ __device__ __forceinline__ void write_summary_warp(const DegPartial (&p)[kMaxDeg
     res->n_deg = n_deg;
     res->map_deg = min_deg + best;
     res->status = status;
+    res->pad = 0;  // every field is written: callers need not clear the result
   }
 }
 
