@@ -46,23 +46,37 @@ KERNELS_PER_STEP = 2  # trace (normalisation and posterior fused), resampling (g
 # a kernel changed since its capture reports traffic null instead of a stale
 # number.
 MEASURED_TRAFFIC = {
-    "poly_trace_tc_kernel": {"bytes": 245248 + 538769408, "source": "trace_tc.cu",
-                             "sha256": "d1b865959934003f"},
-    "resample_coop_kernel": {"bytes": 68295424 + 546867456, "source": "resample_coop.cu",
-                             "sha256": "048ef78ecca62396"},
+    "poly_trace_tc_kernel": {"bytes": 171562 + 538914645,
+                             "sources": ["trace_tc.cu", "trace.cuh", "suffstat.cuh", "posterior.cuh",
+                                         "dfloat.cuh", "poly.cuh", "rng.cuh", "kernels.h",
+                                         "common.cuh"],
+                             "sha256": "d685a6d2100d8275"},
+    "resample_coop_kernel": {"bytes": 68292778 + 547200725,
+                             "sources": ["resample_coop.cu", "gridsync.cuh", "fixedpoint.cuh",
+                                         "rng.cuh", "kernels.h", "common.cuh"],
+                             "sha256": "d29ef8faeea6a3a0"},
 }
 
 
-def measured_traffic(kernel):
-    """The captured DRAM bytes of `kernel`, or None when its source changed."""
+def source_digest(sources):
+    """First 16 hex digits of the SHA-256 of the kernel's source files (its .cu
+    and every header it includes), in the listed order."""
     import hashlib
+    h = hashlib.sha256()
+    for name in sources:
+        with open(os.path.join(ROOT, "paper_2010_08454_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel):
+    """The captured DRAM bytes of `kernel`, or None when any of its sources
+    changed since the capture."""
     ent = MEASURED_TRAFFIC.get(kernel)
     if not ent or ent["bytes"] is None or ent["sha256"] is None:
         return None
-    path = os.path.join(ROOT, "paper_2010_08454_gb300", "csrc", ent["source"])
     try:
-        with open(path, "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()[:16]
+        digest = source_digest(ent["sources"])
     except OSError:
         return None
     return ent["bytes"] if digest == ent["sha256"] else None
