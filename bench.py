@@ -41,10 +41,10 @@ WORKLOAD = ("linefitting likelihood weighting, 2^24 particles x 256 points, degr
 KERNELS_PER_STEP = 2  # trace (normalisation and posterior fused), resampling (gather fused)
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # each of the step's kernels on the default workload, from an ncu capture of
-# that kernel, with the SHA-256 prefix of the source file it was built from.
-# bench.py reports a figure only while the source still has that digest, so
-# a kernel changed since its capture reports traffic null instead of a stale
-# number.
+# that kernel, with the SHA-256 prefix of the source files it was built from
+# (its .cu and the headers it includes).  bench.py reports a figure only while
+# the sources still have that digest, so a changed kernel reads null until it
+# is captured again.
 MEASURED_TRAFFIC = {
     "poly_trace_tc_kernel": {"bytes": 171562 + 538914645,
                              "sources": ["trace_tc.cu", "trace.cuh", "suffstat.cuh", "posterior.cuh",

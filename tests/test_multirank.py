@@ -64,3 +64,18 @@ def test_reference_arm_other_ranks_exit_without_work():
                        capture_output=True, text=True, timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_traffic_figures_only_for_unchanged_kernel_sources(monkeypatch):
+    """The DRAM traffic the bench line reports comes from an ncu capture; it is
+    reported only while every source file of the kernel still has the digest
+    recorded with the capture, and a changed source makes it null."""
+    import bench
+    for name, ent in bench.MEASURED_TRAFFIC.items():
+        assert ent["sources"][0].endswith(".cu")
+        want = ent["bytes"] if bench.source_digest(ent["sources"]) == ent["sha256"] else None
+        assert bench.measured_traffic(name) == want
+        stale = dict(ent, sha256="0" * 16)
+        monkeypatch.setitem(bench.MEASURED_TRAFFIC, name, stale)
+        assert bench.measured_traffic(name) is None
+    assert bench.measured_traffic("no_such_kernel") is None
