@@ -46,15 +46,15 @@ KERNELS_PER_STEP = 2  # trace (normalisation and posterior fused), resampling (g
 # the sources still have that digest, so a changed kernel reads null until it
 # is captured again.
 MEASURED_TRAFFIC = {
-    "poly_trace_tc_kernel": {"bytes": 171562 + 538914645,
+    "poly_trace_tc_kernel": {"bytes": 220928 + 538937301,
                              "sources": ["trace_tc.cu", "trace.cuh", "suffstat.cuh", "posterior.cuh",
                                          "dfloat.cuh", "poly.cuh", "rng.cuh", "kernels.h",
                                          "common.cuh"],
-                             "sha256": "d685a6d2100d8275"},
-    "resample_coop_kernel": {"bytes": 68292778 + 547200725,
+                             "sha256": "a0d55b64561897cc"},
+    "resample_coop_kernel": {"bytes": 68289664 + 547260074,
                              "sources": ["resample_coop.cu", "gridsync.cuh", "fixedpoint.cuh",
                                          "rng.cuh", "kernels.h", "common.cuh"],
-                             "sha256": "d29ef8faeea6a3a0"},
+                             "sha256": "e372984179a85517"},
 }
 
 
@@ -308,13 +308,28 @@ def bench_smc(torch, ppl, reps=5):
     assert ppl.ppl_workspace_status(ws) == 0
     ms = float(np.median(times))
     logz = float(out["log_z"].item())
+    n_res = int(out["resampled"].sum().item())
+    # the step separators alone: the filter's grid barriers (one per step, two
+    # more per resampling step) at its launch shape, with no work between them
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    per_thread = next(r for r in range(1, 9) if -(-N // (1024 * r)) <= sms)
+    blocks = -(-N // (1024 * per_thread))
+    n_bar = T + 2 * n_res
+    bws = ppl.ppl_grid_barrier_probe(blocks, n_bar)
+    bar_ms = float(np.median([_event_ms(torch, lambda: ppl.ppl_grid_barrier_probe(blocks, n_bar,
+                                                                                  ws=bws), 1)
+                              for _ in range(reps)]))
+    assert ppl.ppl_workspace_status(bws) == 0
     import oracle
     kal = oracle.kalman_logz(oracle.lgssm_model(), y)
     return {"workload": "bootstrap filter, linear-Gaussian SSM, T=200, 2^20 particles, FP32 "
                         "state, resample when ESS < N/2; all 200 steps in one persistent "
                         "cooperative kernel",
             "metric": "particle-steps/sec", "value": N * T / (ms / 1e3), "unit": "particle-steps/s",
-            "ms_per_filter": ms, "resampling_steps": int(out["resampled"].sum().item()),
+            "ms_per_filter": ms, "resampling_steps": n_res,
+            "grid_barriers": {"count": n_bar, "blocks": blocks, "ms_alone": bar_ms,
+                              "us_per_barrier": 1e3 * bar_ms / n_bar,
+                              "frac_of_filter": bar_ms / ms},
             "log_z": logz, "kalman_log_z": kal, "abs_err_vs_kalman": abs(logz - kal),
             "gpu_launches_per_filter": 1,
             "stepwise_graph": {"ms_per_filter": ms_steps, "log_z": logz_steps,

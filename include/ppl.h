@@ -400,6 +400,18 @@ ppl_status ppl_smc_run(const ppl_model* model, const float* y, int32_t T, uint64
                        int32_t* resampled_out, double* ess_out, void* ws, size_t ws_bytes,
                        ppl_stream stream);
 
+/* The cost floor of ppl_smc_run's step separators (§6: the particle filter's
+ * steps meet at population-wide reductions): one cooperative launch of
+ * `blocks` blocks of 1024 threads (the filter's launch shape; 1 <= blocks <=
+ * the SMs) passing n_barriers (>= 1) bounded grid barriers of the filter's
+ * kind and doing nothing else.  The caller times it on `stream` (CUDA events)
+ * to see what the barriers alone cost.  `ws` [dev] holds at least 1024 bytes
+ * (its first 512 are cleared by the call); a barrier wait that runs out
+ * records PPL_ETIMEOUT there (ppl_workspace_status).  Bad sizes ->
+ * PPL_EINVAL. */
+ppl_status ppl_grid_barrier_probe(int32_t blocks, int32_t n_barriers, void* ws, size_t ws_bytes,
+                                  ppl_stream stream);
+
 /* Posterior summary (as ppl_infer_is) of an existing weighted population of
  * line-fitting particles [dev] with log-weights lw [dev]; lw == NULL means
  * equal weights.  Writes *out_dev [dev]. */

@@ -179,6 +179,8 @@ _SIGS = {
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                    ctypes.c_void_p]),
+    "ppl_grid_barrier_probe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                              ctypes.c_size_t, ctypes.c_void_p]),
     "ppl_rng_words": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
                                      ctypes.c_uint32, ctypes.c_int64, ctypes.c_int32,
                                      ctypes.c_void_p, ctypes.c_void_p]),
@@ -577,6 +579,16 @@ def ppl_smc_run(model, y, n, seed, ws=None, out=None, stream=None):
     _check(st, "ppl_smc_run")
     out["ws"] = ws
     return out
+
+
+def ppl_grid_barrier_probe(blocks, n_barriers, ws=None, stream=None):
+    """n_barriers grid barriers of the filter's kind, nothing else; returns ws."""
+    if ws is None:
+        ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    st = lib().ppl_grid_barrier_probe(int(blocks), int(n_barriers), _ptr(ws), ws.numel(),
+                                      _stream(stream))
+    _check(st, "ppl_grid_barrier_probe")
+    return ws
 
 
 def ppl_rng_words(seed, instance, step, purpose, n_particles, n_blocks, out=None, stream=None):

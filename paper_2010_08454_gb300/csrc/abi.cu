@@ -466,6 +466,14 @@ ppl_status ppl_smc_run(const ppl_model* model, const float* y, int32_t T, uint64
   return cuda_status(e);
 }
 
+ppl_status ppl_grid_barrier_probe(int32_t blocks, int32_t n_barriers, void* ws, size_t ws_bytes,
+                                  ppl_stream stream) {
+  if (blocks < 1 || blocks > num_sms() || n_barriers < 1 || n_barriers > (1 << 27) || !ws ||
+      ws_bytes < 1024 || (reinterpret_cast<uintptr_t>(ws) % kAlign))
+    return PPL_EINVAL;
+  return cuda_status(launch_grid_barrier_probe(blocks, n_barriers, ws, (cudaStream_t)stream));
+}
+
 ppl_status ppl_posterior_reduce(const ppl_model* model, const ppl_poly_particle* particles,
                                 const float* lw, int64_t n, ppl_is_result* out_dev, void* ws,
                                 size_t ws_bytes, ppl_stream stream) {

@@ -140,6 +140,7 @@ cudaError_t launch_smc_persistent(const LgssmParams& p, const float* y, int32_t 
                                   int64_t N, float* x_out, float* lw_out, double* logz,
                                   int32_t* resampled, double* ess, char* ws, size_t ws_bytes,
                                   int32_t** status_out, cudaStream_t s);
+cudaError_t launch_grid_barrier_probe(int blocks, int n_barriers, void* ws, cudaStream_t s);
 cudaError_t launch_smc_commit(float* x, const float* x_tmp, float* lw, int64_t N,
                               const int32_t* gate, cudaStream_t s);
 

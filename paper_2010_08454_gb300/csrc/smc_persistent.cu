@@ -402,6 +402,25 @@ __global__ void __launch_bounds__(kSmcTpb, 1) smc_persistent_kernel(SmcArgs a) {
     }
 }
 
+// The filter's grid barriers with nothing between them: what the step
+// separators alone cost at the filter's launch shape.
+__global__ void __launch_bounds__(kSmcTpb) grid_barrier_probe_kernel(SmcCtl* ctl, int n) {
+  __shared__ unsigned long long rel;
+  for (int e = 1; e <= n; ++e)
+    if (!grid_sync<false>(&ctl->g, &ctl->status, gridDim.x, (unsigned long long)e, &rel,
+                          [] { return 0ull; }, [] {}))
+      return;
+}
+
+cudaError_t launch_grid_barrier_probe(int blocks, int n_barriers, void* ws, cudaStream_t s) {
+  SmcCtl* ctl = static_cast<SmcCtl*>(ws);
+  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(SmcCtl), s);
+  if (e != cudaSuccess) return e;
+  void* args[] = {&ctl, &n_barriers};
+  return cudaLaunchCooperativeKernel((const void*)grid_barrier_probe_kernel, dim3((unsigned)blocks),
+                                     dim3(kSmcTpb), args, 0, s);
+}
+
 size_t smc_run_workspace(int64_t N, int64_t T) {
   return 8 * 256 + (size_t)kSmcMaxGrid * (sizeof(SmcPart) + 3 * 8) + 8 +
          (size_t)std::max<int64_t>(T, 0) * sizeof(SmcStep) + (size_t)N * 4;

@@ -17,8 +17,8 @@
 // dropped A_lo B_lo is below 2^-22 of each product.  The powers x^k are
 // formed in FP64 before their split, and y is carried exactly by the two
 // columns (yh, yr).  The sum of squares is taken in FP32 by each trace's
-// thread (eight running sums in f32x2 pairs per 64-point block, a
-// compensated sum across blocks).
+// thread (eight running sums in f32x2 pairs per 64-point block; the block
+// sums add plainly up to 512 points, with Kahan's compensation beyond).
 //
 // Layout: one CTA per SM; its four warpgroups hold all 512 tensor-memory
 // columns, 128 FP32 columns of D each.  Warpgroup g takes tiles g, g + 4, ..
@@ -326,6 +326,10 @@ __device__ __forceinline__ void fold_warp(DegPartial* wr, float lw, int d, int i
 
 }  // namespace
 
+// kComp: the 64-point block sums of a trace add with Kahan's compensation
+// (data sets above 512 points) or plainly (at most 7 additions: below 2^-21
+// relative).
+template <bool kComp>
 __global__ void __launch_bounds__(kTcThreads, 1) poly_trace_tc_kernel(
     PolyParams p, const float* __restrict__ xs, const float* __restrict__ ys, int L, int Lp,
     int64_t N, int64_t first, uint64_t seed, uint32_t instance, float* __restrict__ lw_out,
@@ -479,7 +483,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) poly_trace_tc_kernel(
         }
         const float2 a01 = f2_unpack(f2_add(acc[0], acc[1]));
         const float2 a23 = f2_unpack(f2_add(acc[2], acc[3]));
-        kahan_add(ss, comp, (a01.x + a01.y) + (a23.x + a23.y));
+        const float block = (a01.x + a01.y) + (a23.x + a23.y);
+        if (kComp) kahan_add(ss, comp, block);
+        else ss += block;
       }
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       if (j + 1 < n_chunks &&
@@ -571,19 +577,26 @@ cudaError_t launch_poly_trace_tc(const PolyParams& p, const float* x, const floa
   const size_t smem = trace_tc_smem(L);
   // the largest shared-memory size, once per device (the attribute is per
   // device; setting it is a slow host call)
+  const bool comp = Lp > 4 * kTcChunk;
+  const void* fn = comp ? (const void*)poly_trace_tc_kernel<true>
+                        : (const void*)poly_trace_tc_kernel<false>;
   int unused = 0;
-  cudaError_t e = device_once((const void*)poly_trace_tc_kernel, &unused, [](int*) {
-    return cudaFuncSetAttribute(poly_trace_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = device_once(fn, &unused, [fn](int*) {
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)trace_tc_smem(kTcMaxPoints));
   });
   if (e != cudaSuccess) return e;
   const int64_t tiles = (N + kTcM - 1) / kTcM;
   const int grid = (int)std::max<int64_t>(
       1, std::min<int64_t>((tiles + kTcWGs - 1) / kTcWGs, num_sms()));
-  poly_trace_tc_kernel<<<grid, kTcThreads, smem, s>>>(p, x, y, (int)L, Lp, N, first, seed,
-                                                      instance, lw_out, rec_out, hdr,
-                                                      (DegPartial*)parts, res,
-                                                      (IsPartial*)part_out);
+  if (comp)
+    poly_trace_tc_kernel<true><<<grid, kTcThreads, smem, s>>>(
+        p, x, y, (int)L, Lp, N, first, seed, instance, lw_out, rec_out, hdr, (DegPartial*)parts,
+        res, (IsPartial*)part_out);
+  else
+    poly_trace_tc_kernel<false><<<grid, kTcThreads, smem, s>>>(
+        p, x, y, (int)L, Lp, N, first, seed, instance, lw_out, rec_out, hdr, (DegPartial*)parts,
+        res, (IsPartial*)part_out);
   return cudaGetLastError();
 }
 

@@ -101,3 +101,18 @@ def test_persistent_filter_matches_stepwise_and_oracle(ppl, orc, N, T):
     assert abs(float(out["log_z"].item()) - g["log_z"]) < 1e-6 * T
     r = orc.smc_lgssm(orc.lgssm_model(), y, N, 7, state_f32=True)
     assert abs(float(out["log_z"].item()) - r["log_z"]) <= 1e-3
+
+
+def test_grid_barrier_probe_passes_its_barriers_and_checks_sizes(ppl):
+    """The probe behind the bench's barrier floor: the filter's launch shape
+    (one 1024-thread block per SM) passes its barriers with a clean status;
+    more blocks than SMs, or no barrier, is refused before any launch."""
+    import torch
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    ws = ppl.ppl_grid_barrier_probe(sms, 200)
+    torch.cuda.synchronize()
+    assert ppl.ppl_workspace_status(ws) == 0
+    for blocks, n in ((sms + 1, 10), (1, 0), (0, 10)):
+        with pytest.raises(ppl.PplError) as err:
+            ppl.ppl_grid_barrier_probe(blocks, n, ws=ws)
+        assert err.value.status == ppl.PPL_EINVAL
