@@ -46,12 +46,12 @@ KERNELS_PER_STEP = 2  # trace (normalisation and posterior fused), resampling (g
 # the sources still have that digest, so a changed kernel reads null until it
 # is captured again.
 MEASURED_TRAFFIC = {
-    "poly_trace_tc_kernel": {"bytes": 220928 + 538937301,
+    "poly_trace_tc_kernel": {"bytes": 142293 + 538847232,
                              "sources": ["trace_tc.cu", "trace.cuh", "suffstat.cuh", "posterior.cuh",
                                          "dfloat.cuh", "poly.cuh", "rng.cuh", "kernels.h",
                                          "common.cuh"],
-                             "sha256": "a0d55b64561897cc"},
-    "resample_coop_kernel": {"bytes": 68289664 + 547260074,
+                             "sha256": "8ff769919b56dab1"},
+    "resample_coop_kernel": {"bytes": 68362282 + 547657045,
                              "sources": ["resample_coop.cu", "gridsync.cuh", "fixedpoint.cuh",
                                          "rng.cuh", "kernels.h", "common.cuh"],
                              "sha256": "e372984179a85517"},

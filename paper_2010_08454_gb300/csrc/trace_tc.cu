@@ -12,7 +12,9 @@
 // degree (the cost the paper reports for its GPU code, §5.1).
 //
 // Accuracy: each FP32 operand v is split into two TF32 parts, v = hi + lo
-// (both rounded to nearest), and D accumulates A_hi B_hi + A_hi B_lo +
+// (hi rounded to nearest; the data's lo rounded to nearest, a coefficient's
+// lo = v - hi passed exactly as FP32, of which the tensor cores use the TF32
+// part: within 2^-21 of v), and D accumulates A_hi B_hi + A_hi B_lo +
 // A_lo B_hi in FP32 in tensor memory (three kind::tf32 MMAs of K = 8); the
 // dropped A_lo B_lo is below 2^-22 of each product.  The powers x^k are
 // formed in FP64 before their split, and y is carried exactly by the two
@@ -176,7 +178,7 @@ __device__ __forceinline__ void write_a_row(unsigned char* a_hi, unsigned char* 
   for (int k = 0; k < kMaxCoef; ++k) {
     const float v = valid ? c[k] : 0.0f;
     h[k] = tf32_rna(v);
-    l[k] = tf32_rna(v - h[k]);
+    l[k] = v - h[k];  // exact; the tensor cores read its TF32 part
   }
   h[6] = h[7] = valid ? 1.0f : 0.0f;  // the y columns
   l[6] = l[7] = 0.0f;
