@@ -80,7 +80,9 @@ typedef struct {
   uint32_t origin;
 } ppl_poly_particle;
 
-/* Posterior summary of a weighted population (§3.6.2, Fig. 1).  FP64.
+/* Posterior summary of a weighted population (§3.6.2, Fig. 1).  FP64 fields,
+ * formed from FP32 partials with double-float sums (about 48 significant
+ * bits); the kernels write every field, so the buffer needs no clearing.
  *  log_z   = lse - log N: estimate of the evidence E_prior[exp(sum of factors)]
  *  ess     = (sum w)^2 / sum w^2
  *  argmax  = the mode: index of the highest log-weight (lowest index on ties)
@@ -198,7 +200,7 @@ ppl_status ppl_infer_is_partial(const ppl_model* model, const ppl_data* data,
 /* The summary of a population from its shards' partials, partials_dev [dev,
  * n_partials] (e.g. gathered from every rank), into *out_dev [dev].  The
  * result is that of ppl_infer_is_instance on the whole population up to the
- * order of FP32/FP64 roundings in the merge (maxima, argmax and counts are
+ * order of FP32 and double-float roundings in the merge (maxima, argmax and counts are
  * exact).  A shard's device error is reported in out_dev->status; no finite
  * weight anywhere -> PPL_EEMPTY. */
 ppl_status ppl_is_merge(const ppl_is_partial* partials_dev, int32_t n_partials,

@@ -441,7 +441,7 @@ __device__ __forceinline__ void finalize_partials(const DegPartial* parts, int G
 // ---------------------------------------------------------------------------
 // One shard's share of a likelihood-weighting pass whose particles are split
 // over several devices: its per-degree partials merged (FP32 means and
-// second moments, FP64 sums around each degree's maximum), its particle
+// second moments, double-float sums around each degree's maximum), its particle
 // count and device status.  Shards merge exactly like blocks (§3.6.2: the
 // normalisation runs over all samples, wherever they were drawn).
 // ---------------------------------------------------------------------------
