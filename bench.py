@@ -50,7 +50,7 @@ MEASURED_TRAFFIC = {
                              "sources": ["trace_tc.cu", "trace.cuh", "suffstat.cuh", "posterior.cuh",
                                          "dfloat.cuh", "poly.cuh", "rng.cuh", "kernels.h",
                                          "common.cuh"],
-                             "sha256": "8ff769919b56dab1"},
+                             "sha256": "b4edf735f915de97"},
     "resample_coop_kernel": {"bytes": 68362282 + 547657045,
                              "sources": ["resample_coop.cu", "gridsync.cuh", "fixedpoint.cuh",
                                          "rng.cuh", "kernels.h", "common.cuh"],
