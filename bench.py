@@ -533,11 +533,17 @@ def bench_batched(torch, ppl, reps=5):
     n_traces = int(inst["part_off"][-1])
     # expected FP32 flops of the factor under the degree prior: (2 ncoef + 1), mean ncoef 4.5
     flops = float(plan.work) * 10.0
+    peaks = load_peaks()
+    fp32_peak = (torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2 *
+                 (peaks or {}).get("sm_max_mhz", 2070.0) * 1e6 / 1e12)
     return {"workload": "4096 line-fitting instances, data lengths log-uniform [16, 4096], "
                         "particles log-uniform [2^10, 2^16], one persistent launch in a CUDA graph",
             "metric": "particle-traces/sec", "value": n_traces / (ms / 1e3), "unit": "traces/s",
             "ms_per_launch": ms, "traces": n_traces, "trace_points": float(plan.work),
             "fp32_tflops": flops / (ms / 1e3) / 1e12,
+            # against the FP32 FMA peak: SMs x 128 lanes x 2 FLOP x max SM clock
+            "fp32_peak_tflops": fp32_peak,
+            "frac": flops / (ms / 1e3) / 1e12 / fp32_peak,
             "autotuned": {"ppt": plan.ppt, "blocks_per_sm": plan.blocks_per_sm},
             "items": int(plan.n_items), "status": status}
 
