@@ -17,8 +17,8 @@ struct ProposalSmem {
   float cum[kMaxDegrees];
   float logq[kMaxDegrees];
   int base[kMaxDegrees];
-  float mu[kMaxSlots], s[kMaxSlots], logs[kMaxSlots];
-  float log_p, log_sigma, sigma;
+  float mu[kMaxSlots], s[kMaxSlots], logs[kMaxSlots], inv_s[kMaxSlots];
+  float log_p, log_sigma, sigma, inv_sigma;
 };
 
 // Proposal of one data set from its 48 network outputs (one thread).
@@ -45,18 +45,23 @@ __device__ __forceinline__ void load_proposal(const PolyParams& p, const float* 
     }
   }
   ps.sigma = p.prior_sigma;
+  ps.inv_sigma = 1.0f / p.prior_sigma;
   ps.log_sigma = logf(p.prior_sigma);
   ps.log_p = -logf((float)p.n_deg);
   for (int i = 0; i < kMaxSlots && i < base; ++i) {
     const float t = fminf(fmaxf(o[5 + 2 * i], -9.0f), 1.0f);
     ps.mu[i] = p.prior_sigma * o[4 + 2 * i];
     ps.s[i] = p.prior_sigma * expf(t);
+    ps.inv_s[i] = 1.0f / ps.s[i];  // (the prior's reciprocal when s equals sigma)
     ps.logs[i] = ps.log_sigma + t;
   }
 }
 
-__device__ __forceinline__ float log_normal32(float x, float mu, float s, float logs) {
-  const float z = (x - mu) / s;
+// log N(x; mu, s^2) with 1/s given (one multiply instead of a division, in
+// the same form for the prior and the proposal, so a proposal equal to the
+// prior cancels exactly)
+__device__ __forceinline__ float log_normal32(float x, float mu, float inv_s, float logs) {
+  const float z = (x - mu) * inv_s;
   return -0.918938533f - logs - 0.5f * z * z;
 }
 
@@ -72,13 +77,12 @@ struct LearnedDraw {
     box_muller(a.x, a.y, z[0], z[1]);
     box_muller(a.z, a.w, z[2], z[3]);
     box_muller(b.x, b.y, z[4], z[5]);
+    // the inverse CDF of q at u: the first degree whose cumulative mass
+    // exceeds u (the last one when rounding leaves u above every mass)
     const float u = u01(b.z);
-    int k = p.n_deg - 1;
-    for (int kk = 0; kk < p.n_deg; ++kk)
-      if (u < ps->cum[kk]) {
-        k = kk;
-        break;
-      }
+    int k = 0;
+#pragma unroll
+    for (int kk = 0; kk < kMaxDegrees - 1; ++kk) k += (kk < p.n_deg - 1 && u >= ps->cum[kk]);
     const int n = p.min_deg + k, ncoef = n + p.coef_offset, base = ps->base[k];
     float cr = ps->log_p - ps->logq[k];
 #pragma unroll
@@ -86,8 +90,8 @@ struct LearnedDraw {
       if (j < ncoef) {
         const float mu = ps->mu[base + j], s = ps->s[base + j];
         c[j] = fmaf(s, z[j], mu);
-        cr += log_normal32(c[j], 0.0f, ps->sigma, ps->log_sigma) -
-              log_normal32(c[j], mu, s, ps->logs[base + j]);
+        cr += log_normal32(c[j], 0.0f, ps->inv_sigma, ps->log_sigma) -
+              log_normal32(c[j], mu, ps->inv_s[base + j], ps->logs[base + j]);
       } else {
         c[j] = 0.0f;
       }
