@@ -548,7 +548,7 @@ def bench_batched(torch, ppl, reps=5):
             "items": int(plan.n_items), "status": status}
 
 
-def bench_learned(torch, ppl, epochs=4, n_sets=1024, N=1 << 20, reps=3):
+def bench_learned(torch, ppl, epochs=4, n_sets=1024, N=1 << 20, reps=3, n_pairs=1 << 22):
     """Learned vs prior proposal: ESS/sec at |delta log Z| < 0.05 on held-out data sets."""
     import numpy as np
 
@@ -557,7 +557,7 @@ def bench_learned(torch, ppl, epochs=4, n_sets=1024, N=1 << 20, reps=3):
     model = ppl.poly_model()
     params = ppl.pack_params(synth.mlp_weights(1))
     am, av = torch.zeros_like(params), torch.zeros_like(params)
-    n_pairs, batch = 1 << 20, 1024
+    batch = 1024
     steps = epochs * (n_pairs // batch)
     block = 64  # training steps per CUDA graph replay
     pws = ppl.proposal_workspace(batch)
