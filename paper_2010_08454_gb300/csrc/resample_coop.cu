@@ -10,7 +10,8 @@
 //      -- chunk c holds the ancestors of outputs [K_c, K_c+1) -- and cuts each
 //      chunk's outputs into work items of at most 256;
 //   3. each block takes a contiguous run of items (weighted so that a chunk's
-//      prefix sums count as a number of items); for each chunk the run
+//      prefix sums count as a number of items; a run never ends inside a
+//      chunk with at most two outputs per particle); for each chunk the run
 //      touches, the block forms the chunk's inclusive prefix sums in shared
 //      memory (lw is L2-resident by now) with a two-level index of every 8th
 //      and every 256th sum, and then its warps take the chunk's items
@@ -512,10 +513,37 @@ __global__ void __launch_bounds__(kRcTpb, 2) resample_coop_kernel(RcArgs a) {
   // of cost units and walks it chunk by chunk.  Chunk c's units are
   // [ioff_c, ioff_c+1): kRcPrefixCost that stand for its prefix sums, then one
   // per item; a run that holds none of the chunk's items skips the chunk.
-  const int64_t it1 = n_items * (blockIdx.x + 1) / G;
+  // An end of the run that falls inside a chunk with at most kRcScatterOut
+  // outputs moves to the nearer end of that chunk (block b's last end is
+  // block b + 1's first, moved the same way), so such a chunk is never split
+  // between two blocks: one block builds its prefix sums and writes it in the
+  // scatter form.  Moving the ends is monotone, so the runs still tile the
+  // units in order.
+  int64_t it1 = n_items * (blockIdx.x + 1) / G;
   int32_t* sWw = sW + warp * kRcItemOut;
   int64_t it = n_items * blockIdx.x / G;
-  if (warp == 0 && it < it1) seg_lookup(a, it, -1, seg_sh[0], lane);
+  {
+    __shared__ int64_t ends[2];
+    if (warp < 2) {  // warp 0 the first end, warp 1 the last
+      int64_t x = warp == 0 ? it : it1;
+      if (x > 0 && x < n_items) {
+        seg_lookup(a, x, -1, seg_sh[warp], lane);
+        __syncwarp();
+        const int64_t io0 = seg_sh[warp][1], io1 = seg_sh[warp][2];
+        if (seg_sh[warp][4] - seg_sh[warp][3] <= kRcScatterOut)
+          x = 2 * (x - io0) <= io1 - io0 ? io0 : io1;
+      }
+      if (lane == 0) ends[warp] = x;
+    }
+    __syncthreads();
+    // warp 0's descriptor is the first chunk's unless the first end moved
+    // (or was not looked up)
+    const bool again = ends[0] != it || it == 0;
+    it = ends[0];
+    it1 = ends[1];
+    __syncthreads();  // seg_sh[1] is the next chunk's slot from here on
+    if (warp == 0 && it < it1 && again) seg_lookup(a, it, -1, seg_sh[0], lane);
+  }
   __syncthreads();
   for (int cur = 0; it < it1; cur ^= 1) {
     const int64_t ch = seg_sh[cur][0], io0 = seg_sh[cur][1];

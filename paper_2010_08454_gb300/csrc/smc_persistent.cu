@@ -8,13 +8,17 @@
 // both give the same particles.
 //
 // A step is: propagate and weight (registers) -> block partial -> barrier 1,
-// whose last arriving block merges the partials and takes the resampling
-// decision for everyone (published in the release word itself); when
-// resampling: fixed-point weights and block totals -> barrier 2, whose last
-// block scans the totals and tells every block which output slots its
-// particles are the ancestors of -> each block finds those ancestors by a
-// merge of its prefix sums with the slots' positions, in shared memory, and
-// writes the slots -> barrier 3 -> every thread reads its slots.
+// after which every block merges all the partials itself, in one fixed order,
+// so that all take the same resampling decision; when resampling: fixed-point
+// weights and block totals -> barrier 2, after which every block scans all
+// the totals itself and finds which output slots its particles are the
+// ancestors of -> each block finds those ancestors by a merge of its prefix
+// sums with the slots' positions, in shared memory, and writes the slots ->
+// barrier 3 -> every thread reads its slots.  The three barriers are plain
+// arrival counts: a merge or scan done once by the last arriving block and
+// published to the others would add its own latency and that of the release
+// to every step, for a few kilobytes that every block reads from L2 in one
+// round trip.
 //
 // Every barrier wait is bounded; a block whose wait runs out records
 // PPL_ETIMEOUT and every block leaves at its next wait, so the kernel always
@@ -51,8 +55,6 @@ struct __align__(16) SmcStep {
 
 // Control block at offset 0 of the workspace: the status word (first, where
 // ppl_workspace_status reads it) on its own line, then the barrier words.
-// Barrier 1's payload in the release word is bad << 33 | resample << 32 |
-// bits of M; barrier 2 publishes T, the stride and u.
 struct __align__(128) SmcCtl {
   int32_t status;
   int32_t pad[31];
@@ -71,10 +73,8 @@ struct SmcArgs {
   int32_t* resampled;  // [T]
   double* ess;         // [T]
   SmcCtl* ctl;
-  SmcPart* parts;      // [grid]
+  SmcPart* parts;      // [2][grid] block partials of even and odd steps
   uint64_t* bsum;      // [grid] block totals of the fixed-point weights
-  uint64_t* bexcl;     // [grid] their exclusive prefix
-  int64_t* kstart;     // [grid + 1] first output slot whose ancestor each block holds
   SmcStep* stash;      // [T]
   float* xbuf;         // [N] the resampled states, by output slot
 };
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(kSmcTpb, 1) smc_persistent_kernel(SmcArgs a) {
   __shared__ double sh_z[kSmcWarps];
   __shared__ unsigned long long rel;
   __shared__ uint64_t view[6];  // T, stride, u, C at the block start, K_b, K_b+1
-  __shared__ uint64_t j_view[2];
+  __shared__ unsigned long long decision;  // bad << 33 | resample << 32 | bits of M
   __shared__ uint32_t resample_word;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const unsigned G = gridDim.x;
@@ -122,6 +122,11 @@ __global__ void __launch_bounds__(kSmcTpb, 1) smc_persistent_kernel(SmcArgs a) {
     if (tid == 0) resample_word = philox_block(a.seed, 0, 0, (uint32_t)t, kResample, 0).x;
     const float yt = y_next;
     if (t < a.T) y_next = __ldg(a.y + t);  // in flight during this step
+    // this step's half of the partials: a block may write step t + 1's
+    // partial while slower blocks still read step t's, but not step t + 2's
+    // (it has to pass barrier 1 of step t + 1 first, which they reach only
+    // after reading)
+    SmcPart* const parts_t = a.parts + (size_t)(t & 1) * G;
     int nan = 0;
     float tm = -INFINITY;
 #pragma unroll
@@ -174,15 +179,17 @@ __global__ void __launch_bounds__(kSmcTpb, 1) smc_persistent_kernel(SmcArgs a) {
         q.s = bs;
         q.s2 = bs2;
         q.nan = bn;
-        *reinterpret_cast<float4*>(a.parts + blockIdx.x) = *reinterpret_cast<const float4*>(&q);
+        *reinterpret_cast<float4*>(parts_t + blockIdx.x) = *reinterpret_cast<const float4*>(&q);
       }
     }
-    // barrier 1: the last block merges all partials in a fixed order and
-    // publishes the maximum and the decision in the release word
-    const bool ok1 = grid_sync<true>(&ctl->g, &ctl->status, G, ++e, &rel, [&]() -> unsigned long long {
+    // barrier 1, then every block merges all partials in the same fixed order
+    // (thread b reads block b's): the maximum M, the sums around it as
+    // double-float pairs, the NaN and empty checks and the decision
+    if (!grid_sync<false>(&ctl->g, &ctl->status, G, ++e, &rel, [] { return 0ull; }, [] {})) return;
+    {
       SmcPart q;
       if ((unsigned)tid < G) {
-        const float4 v = __ldcg(reinterpret_cast<const float4*>(a.parts + tid));
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(parts_t + tid));
         q = *reinterpret_cast<const SmcPart*>(&v);
       } else {
         q.m = -INFINITY;
@@ -211,7 +218,6 @@ __global__ void __launch_bounds__(kSmcTpb, 1) smc_persistent_kernel(SmcArgs a) {
         j_s2[warp] = Ss2;
       }
       __syncthreads();
-      unsigned long long payload = 0;
       if (warp == 0) {
         Ss = df_warp_sum(j_s[lane]);
         Ss2 = df_warp_sum(j_s2[lane]);
@@ -221,25 +227,26 @@ __global__ void __launch_bounds__(kSmcTpb, 1) smc_persistent_kernel(SmcArgs a) {
           const bool bad = any_nan || !(M > -INFINITY);
           const bool res =
               !bad && __fadd_rn(__fsub_rn(lhs.x, rhs.x), __fsub_rn(lhs.y, rhs.y)) < 0.0f;
-          if (any_nan) record_status(&ctl->status, PPL_ENAN);
-          else if (bad) record_status(&ctl->status, PPL_EEMPTY);
-          SmcStep st;
-          st.M = M;
-          st.s_hi = Ss.x;
-          st.s_lo = Ss.y;
-          st.s2_hi = Ss2.x;
-          st.s2_lo = Ss2.y;
-          st.flag = res ? 1 : 0;
-          st.pad[0] = st.pad[1] = 0;
-          a.stash[t - 1] = st;
-          payload = ((unsigned long long)bad << 33) | ((unsigned long long)res << 32) |
-                    (unsigned long long)__float_as_uint(M);
+          if (blockIdx.x == 0) {  // one block records the step
+            if (any_nan) record_status(&ctl->status, PPL_ENAN);
+            else if (bad) record_status(&ctl->status, PPL_EEMPTY);
+            SmcStep st;
+            st.M = M;
+            st.s_hi = Ss.x;
+            st.s_lo = Ss.y;
+            st.s2_hi = Ss2.x;
+            st.s2_lo = Ss2.y;
+            st.flag = res ? 1 : 0;
+            st.pad[0] = st.pad[1] = 0;
+            a.stash[t - 1] = st;
+          }
+          decision = ((unsigned long long)bad << 33) | ((unsigned long long)res << 32) |
+                     (unsigned long long)__float_as_uint(M);
         }
       }
-      return payload;
-    }, [] {});
-    if (!ok1) return;
-    const unsigned long long r1 = rel;
+      __syncthreads();
+    }
+    const unsigned long long r1 = decision;
     if ((r1 >> 33) & 1) return;  // a NaN or no finite weight: every block leaves
     if (!((r1 >> 32) & 1)) continue;
     const float M = __uint_as_float((uint32_t)r1);
@@ -264,46 +271,44 @@ __global__ void __launch_bounds__(kSmcTpb, 1) smc_persistent_kernel(SmcArgs a) {
       btot = __shfl_sync(0xffffffffu, wi, 31);
     }
     if (tid == 0) a.bsum[blockIdx.x] = btot;
-    // barrier 2: the last block scans the block totals, draws the systematic
-    // offset u (stride = floor(T / N)) and gives every block b the first output
-    // whose ancestor it holds, K_b = cnt(C at the block's start), where
-    // cnt(c) = #{k >= 0 : u + k stride < c}
-    const bool ok2 = grid_sync<true>(&ctl->g, &ctl->status, G, ++e, &rel, [&]() -> unsigned long long {
+    // barrier 2, then every block scans the G block totals itself (the same
+    // integer sums in every block): T, the stride floor(T / N), the systematic
+    // offset u, and the first outputs whose ancestors this block and the next
+    // hold, K_b = cnt(C at the block's start), where cnt(c) = #{k >= 0 : u + k
+    // stride < c} (K_G = N)
+    if (!grid_sync<false>(&ctl->g, &ctl->status, G, ++e, &rel, [] { return 0ull; }, [] {})) return;
+    {
       const uint64_t v = (unsigned)tid < G ? __ldcg(a.bsum + tid) : 0ull;
       const uint64_t wi = warp_scan_u64(v, lane);
       if (lane == 31) j_tot[warp] = wi;
       __syncthreads();
       const uint64_t jv = j_tot[lane], ji = warp_scan_u64(jv, lane);
-      const uint64_t ex = sat_add(__shfl_sync(0xffffffffu, ji - jv, warp), wi - v);
+      const uint64_t ex = sat_add(__shfl_sync(0xffffffffu, ji - jv, warp), wi - v);  // C at block tid's start
       const uint64_t T = __shfl_sync(0xffffffffu, ji, 31);
       const bool valid = T >= (uint64_t)N && T <= (1ull << 61);
-      if (tid == 0) {
-        const uint64_t stride = valid ? T / (uint64_t)N : 0;
-        const uint64_t w0 = resample_word;
-        if (!valid) record_status(&ctl->status, T == 0 ? PPL_EEMPTY : PPL_EINVAL);
-        j_view[0] = stride;
-        j_view[1] = (__umul64hi(w0, stride) << 32) | ((w0 * stride) >> 32);
-        ctl->g.total = T;
-        ctl->g.stride = j_view[0];
-        ctl->g.offset = j_view[1];
-        a.kstart[G] = N;
+      const unsigned b = blockIdx.x;
+      if ((unsigned)tid == b || (unsigned)tid == b + 1) {  // b + 1 < G <= kSmcTpb when taken
+        uint64_t stride = 0, u = 0;
+        if (valid) {
+          const uint64_t w0 = resample_word;
+          stride = T / (uint64_t)N;
+          u = (__umul64hi(w0, stride) << 32) | ((w0 * stride) >> 32);
+        }
+        const uint64_t k = valid ? (uint64_t)positions_below(ex, u, stride, N) : 0ull;
+        if ((unsigned)tid == b) {
+          view[0] = T;
+          view[1] = stride;
+          view[2] = u;
+          view[3] = ex;
+          view[4] = k;
+          if (b + 1 == G) view[5] = (uint64_t)N;
+        } else if (b + 1 < G) {
+          view[5] = k;
+        }
+        if (b == 0 && tid == 0 && !valid) record_status(&ctl->status, T == 0 ? PPL_EEMPTY : PPL_EINVAL);
       }
       __syncthreads();
-      if (valid && (unsigned)tid < G) {
-        const uint64_t stride = j_view[0], u = j_view[1];
-        a.bexcl[tid] = ex;
-        a.kstart[tid] = positions_below(ex, u, stride, N);
-      }
-      return 0ull;
-    }, [&] {
-      view[0] = __ldcg(&ctl->g.total);
-      view[1] = __ldcg(&ctl->g.stride);
-      view[2] = __ldcg(&ctl->g.offset);
-      view[3] = __ldcg(a.bexcl + blockIdx.x);
-      view[4] = (uint64_t)__ldcg(a.kstart + blockIdx.x);
-      view[5] = (uint64_t)__ldcg(a.kstart + blockIdx.x + 1);
-    });
-    if (!ok2) return;
+    }
     const uint64_t T = view[0];
     if (T < (uint64_t)N || T > (1ull << 61)) return;  // every block sees the same T and leaves
     // 2. systematic resampling of this block's outputs k in [K_b, K_b+1), whose
@@ -422,7 +427,7 @@ cudaError_t launch_grid_barrier_probe(int blocks, int n_barriers, void* ws, cuda
 }
 
 size_t smc_run_workspace(int64_t N, int64_t T) {
-  return 8 * 256 + (size_t)kSmcMaxGrid * (sizeof(SmcPart) + 3 * 8) + 8 +
+  return 8 * 256 + (size_t)kSmcMaxGrid * (2 * sizeof(SmcPart) + 8) +
          (size_t)std::max<int64_t>(T, 0) * sizeof(SmcStep) + (size_t)N * 4;
 }
 
@@ -467,10 +472,8 @@ cudaError_t launch_smc_persistent(const LgssmParams& p, const float* y, int32_t 
     return q;
   };
   a.ctl = reinterpret_cast<SmcCtl*>(take(sizeof(SmcCtl)));
-  a.parts = reinterpret_cast<SmcPart*>(take((size_t)kSmcMaxGrid * sizeof(SmcPart)));
+  a.parts = reinterpret_cast<SmcPart*>(take(2 * (size_t)kSmcMaxGrid * sizeof(SmcPart)));
   a.bsum = reinterpret_cast<uint64_t*>(take((size_t)kSmcMaxGrid * 8));
-  a.bexcl = reinterpret_cast<uint64_t*>(take((size_t)kSmcMaxGrid * 8));
-  a.kstart = reinterpret_cast<int64_t*>(take(((size_t)kSmcMaxGrid + 1) * 8));
   a.stash = reinterpret_cast<SmcStep*>(take((size_t)T * sizeof(SmcStep)));
   a.xbuf = reinterpret_cast<float*>(take((size_t)N * 4));
   if (off > ws_bytes) return cudaErrorInvalidValue;
