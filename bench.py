@@ -51,10 +51,10 @@ MEASURED_TRAFFIC = {
                                          "dfloat.cuh", "poly.cuh", "rng.cuh", "kernels.h",
                                          "common.cuh"],
                              "sha256": "b4edf735f915de97"},
-    "resample_coop_kernel": {"bytes": 68362282 + 547657045,
+    "resample_coop_kernel": {"bytes": 68255829 + 545833685,
                              "sources": ["resample_coop.cu", "gridsync.cuh", "fixedpoint.cuh",
                                          "rng.cuh", "kernels.h", "common.cuh"],
-                             "sha256": "e372984179a85517"},
+                             "sha256": "ca89214dc1a464f8"},
 }
 
 

@@ -60,6 +60,19 @@ constexpr int kRcJobBlk = 8;     // chunk totals the layout job's first pass loa
 constexpr int kRcJobPer = 4;     // chunks per thread in a tile of the layout job
 constexpr int kRcJobTile = kRcTpb * kRcJobPer;
 
+// 16 bytes of log-weights, marked for eviction last from L2: lw is read
+// again after the grid barrier (the prefix sums), while the records gathered
+// in between stream through L2.
+__device__ __forceinline__ float4 ld_f4_evict_last(const float4* ptr) {
+  float4 v;
+  asm volatile(
+      "{\n .reg .b64 pol;\n createpolicy.fractional.L2::evict_last.b64 pol, 1.0;\n"
+      " ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], pol;\n}"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(ptr));
+  return v;
+}
+
 struct RcArgs {
   const float* lw;         // FP32 log-weights, or
   const uint64_t* qf;      // given fixed-point weights
@@ -178,8 +191,8 @@ template <bool FROM_LW>
 __device__ __forceinline__ void load_raw(const RcArgs& a, int64_t base, RawWeights<FROM_LW>& w) {
   if constexpr (FROM_LW) {
     if (base + kRcItems <= a.n && (reinterpret_cast<uintptr_t>(a.lw + base) & 15) == 0) {
-      const float4 x = __ldcg(reinterpret_cast<const float4*>(a.lw + base));
-      const float4 y = __ldcg(reinterpret_cast<const float4*>(a.lw + base) + 1);
+      const float4 x = ld_f4_evict_last(reinterpret_cast<const float4*>(a.lw + base));
+      const float4 y = ld_f4_evict_last(reinterpret_cast<const float4*>(a.lw + base) + 1);
       w.v[0] = x.x; w.v[1] = x.y; w.v[2] = x.z; w.v[3] = x.w;
       w.v[4] = y.x; w.v[5] = y.y; w.v[6] = y.z; w.v[7] = y.w;
     } else {
